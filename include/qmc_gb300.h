@@ -1,0 +1,242 @@
+/*
+ * qmc_gb300.h -- C ABI of a GB300 (sm_103a) implementation of randomly shifted rank-1
+ * lattice quadrature, the quasi-Monte Carlo method of Borowka, Heinrich, Jahn, Jones,
+ * Kerner, Schlenk, "A GPU compatible quasi-Monte Carlo integrator interfaced to pySecDec"
+ * (arXiv:1811.11720).
+ *
+ * The estimator (Sec. 2.1, Eq. (lattice)) is
+ *     Q^(k) = (1/n) sum_{i<n} g({ i z / n + Delta_k }),    Qbar = (1/m) sum_{k<m} Q^(k),
+ * and its error (Eq. (lattice-error)) is sigma = sqrt( sum_k (Q^(k) - Qbar)^2 / (m (m-1)) ),
+ * per real component.  g is the integrand f after the optional PolySingular
+ * variance-reduction map (Sec. 2.4, Eq. (ISfit)) and a periodizing transform (Sec. 2.3).
+ *
+ * Conventions used by every entry point
+ *   - Return value: QMC_OK (0) on success, a negative QMC_ERR_* code otherwise; nothing is
+ *     written to outputs on argument errors.  qmc_strerror() gives a message.
+ *   - Pointers documented as "device" must be CUDA device (or managed) memory on the
+ *     current device; "host" pointers are ordinary host memory.  The caller owns every
+ *     input and output buffer; the library never frees caller memory.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Device entry points only
+ *     enqueue work and return; results are valid after the stream is synchronised.
+ *   - Lattice points are exact: r = i z_j mod n in integer arithmetic and
+ *     u = RN( frac(r/n + D 2^-53) ), the exact rational rounded once to the nearest
+ *     double (ties to even), where the shift Delta_{k,j} = D_{k,j} 2^-53 and D is a 53-bit
+ *     integer.  u can equal 1.0 when the fraction lies within half an ulp of 1.
+ *   - Sums are deterministic: the same inputs and i-range give bit-identical results.
+ */
+#ifndef QMC_GB300_H
+#define QMC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QMC_ABI_VERSION 1
+#define QMC_MAX_DIM 16      /* integration variables per integrand */
+#define QMC_MAX_SHIFTS 1024 /* random shifts m (the paper's maxmperpackage default) */
+#define QMC_MAX_TERMS 512   /* monomials per polynomial (U and F each) */
+
+/* ---- status codes ------------------------------------------------------------------ */
+enum {
+    QMC_OK = 0,
+    QMC_ERR_ARG = -1,        /* NULL pointer, unknown enum, inconsistent sizes          */
+    QMC_ERR_DIM = -2,        /* dim < 1, dim > QMC_MAX_DIM, or dim > table s_max         */
+    QMC_ERR_N = -3,          /* n < 2, n >= 2^63, or no table size >= the request        */
+    QMC_ERR_GENVEC = -4,     /* some z_j = 0 (mod n) or gcd(z_j, n) != 1                  */
+    QMC_ERR_M = -5,          /* m < 2 (sigma undefined) or m > QMC_MAX_SHIFTS            */
+    QMC_ERR_FIT_PARAMS = -6, /* PolySingular a0 < 1.001 or a1 > -0.001 (Sec. 2.4)         */
+    QMC_ERR_INTEGRAND = -7,  /* unknown family or bad coefficient arrays                 */
+    QMC_ERR_TRANSFORM = -8,  /* unknown transform or orders out of range                 */
+    QMC_ERR_CUDA = -9,       /* a CUDA runtime call failed                               */
+    QMC_ERR_WORKSPACE = -10, /* workspace smaller than qmc_sums_workspace_bytes()         */
+    QMC_ERR_NONFINITE = -11, /* the integrand produced NaN or Inf (result still returned) */
+    QMC_ERR_RANGE = -12,     /* empty or out-of-range i-range / bins                     */
+    QMC_ERR_NO_DEVICE = -13  /* no CUDA device, or the device is not sm_103             */
+};
+
+/* ---- value types -------------------------------------------------------------------- */
+typedef struct { double re, im; } qmc_c64;
+
+/* Result of an integration (the paper's result struct, App. A.2 integrate()). */
+typedef struct {
+    qmc_c64 integral;      /* Qbar (imaginary part 0 for real integrands)              */
+    qmc_c64 error;         /* sigma per component                                     */
+    uint64_t n;            /* size of the last lattice                                  */
+    uint64_t m;            /* shifts of the last lattice                                */
+    uint64_t iterations;   /* lattices evaluated (Case 1 escalation)                    */
+    uint64_t evaluations;  /* integrand evaluations in total                            */
+    uint64_t nonfinite;    /* samples that were NaN or Inf (excluded from nothing)       */
+    uint64_t signfail;     /* complex family: samples with Im F(z) > 0                  */
+} qmc_result;
+
+/* Integrand families.  The paper's integrand is a C++ functor compiled into the kernel
+ * (Sec. 3.2, minimal example); across a C ABI it is described by data instead. */
+enum {
+    QMC_GENZ_OSCILLATORY = 1,   /* cos(2 pi w_1 + sum c_i x_i)          Sec. 5.2 table */
+    QMC_GENZ_PRODUCT_PEAK = 2,  /* prod (c_i^-2 + (x_i - w_i)^2)^-1                 */
+    QMC_GENZ_CORNER_PEAK = 3,   /* (1 + sum c_i x_i)^-(d+1)                         */
+    QMC_GENZ_GAUSSIAN = 4,      /* exp(-sum c_i^2 (x_i - w_i)^2)                   */
+    QMC_GENZ_C0 = 5,            /* exp(-sum c_i |x_i - w_i|)                        */
+    QMC_GENZ_DISCONTINUOUS = 6, /* 0 if x_1 > w_1 or x_2 > w_2 else exp(sum c_i x_i) */
+    QMC_MONOMIAL = 10,          /* prod x_i (the minimal example of Sec. 3.2)       */
+    QMC_TRIG = 11,              /* prod (1 + c_i cos(2 pi (h_i x_i + w_i)))          */
+    QMC_FEYNMAN = 20,           /* complex U(z)^a F(z)^-b det(dz/dx), deformed contour */
+    QMC_SECTOR = 21             /* real U(x)^a F(x)^-b                               */
+};
+
+/* Integrand description.  For host entry points the arrays are host memory, for device
+ * entry points device memory.  Unused arrays may be NULL.
+ *   Genz / trig:  c[dim], w[dim]; trig also h[dim] (integer frequencies).
+ *   Polynomial families: U = sum_m ucoef[m] prod_k x_k^uexp[m*dim+k] (nu terms), F likewise
+ *   (nf terms), exponents 0..15; the value is U^pa F^-pb (principal branch) times, for
+ *   QMC_FEYNMAN, det(dz/dx) at z_k = x_k - i lambda x_k (1 - x_k) dF/dx_k (real x). */
+typedef struct {
+    int family;
+    int dim;
+    const double *c, *w;
+    const int64_t *h;
+    int nu, nf;
+    const double *ucoef, *fcoef;
+    const int32_t *uexp, *fexp;
+    double pa, pb, lambda;
+} qmc_integrand;
+
+/* Periodizing transforms (Sec. 2.3; table of integral transforms, App. A.4). */
+enum { QMC_T_NONE = 0, QMC_T_BAKER = 1, QMC_T_KOROBOV = 2, QMC_T_SIDI = 3 };
+typedef struct {
+    int kind;
+    int r0, r1;   /* Korobov<r0,r1>: weight ~ u^r0 (1-u)^r1, 0 <= r <= 8; Sidi<r0>, 1 <= r0 <= 8 */
+} qmc_transform;
+
+/* Generating-vector table (App. A.1 field generatingvectors; App. A.3): count sizes n[]
+ * in ascending order, row c of z[] (count x s_max, row-major) is the vector for n[c]. */
+typedef struct {
+    const uint64_t *n;
+    const uint64_t *z;
+    int s_max;
+    int count;
+} qmc_genvec_table;
+
+/* One shifted lattice rule with its inputs resident on the device. */
+typedef struct {
+    uint64_t n;                 /* lattice size, 2 <= n < 2^63                          */
+    int dim;                    /* integration variables                                */
+    uint64_t z[QMC_MAX_DIM];    /* generating vector (host copy), gcd(z_j, n) = 1       */
+    uint64_t m;                 /* shifts, 1 <= m <= QMC_MAX_SHIFTS                     */
+    const uint64_t *shifts;     /* device [m][dim] 53-bit integers D, Delta = D 2^-53   */
+    qmc_transform transform;
+    const double *fit;          /* device [dim][6] PolySingular a0..a5 or NULL (no fit) */
+} qmc_rule;
+
+/* Variance-reduction fit options (App. A.1 fields evaluateminn, fitstepsize, fitmaxiter,
+ * fitxtol, fitgtol, fitftol). */
+typedef struct {
+    int enabled;
+    uint64_t evaluateminn;  /* default 100000 */
+    int bins;               /* histogram bins per dimension, default 1000 */
+    int maxiter;            /* default 40 */
+    double xtol, gtol, ftol;/* defaults 3e-3, 1e-8, 1e-8 */
+    int stepsize;           /* every stepsize-th CDF point enters the fit, default 10 */
+} qmc_fit_opts;
+
+/* Error goal for the adaptive mode (App. A.1 fields minn, minm, epsrel, epsabs, maxeval,
+ * errormode). */
+enum { QMC_ERRORMODE_ALL = 0, QMC_ERRORMODE_LARGEST = 1 };
+typedef struct {
+    double epsrel, epsabs;
+    uint64_t maxeval;
+    int errormode;
+} qmc_options;
+
+/* ---- host helpers ------------------------------------------------------------------- */
+const char *qmc_strerror(int code);
+int qmc_abi_version(void);
+
+/* Smallest table size >= preferred (App. A.2 get_next_n).  Errors: QMC_ERR_ARG,
+ * QMC_ERR_N when every size is smaller. */
+int qmc_get_next_n(const qmc_genvec_table *table, uint64_t preferred, uint64_t *n_out);
+
+/* Random shifts (Sec. 2.1: Delta_k i.i.d. uniform on [0,1)^d).  D_out[k*dim + j] (host,
+ * m*dim entries) = output number k*dim + j of the SplitMix64 generator seeded with `seed`,
+ * shifted right by 11 bits.  Errors: QMC_ERR_ARG, QMC_ERR_DIM, QMC_ERR_M. */
+int qmc_make_shifts(uint64_t seed, uint64_t m, int dim, uint64_t *D_out);
+
+/* ---- device entry points (inputs resident on the device) --------------------------- */
+
+/* Lattice points u[(i - i_begin)*m*dim + k*dim + j] for i_begin <= i < i_begin + count
+ * (Eq. (lattice), Fig. 1), written to device memory out[count*m*dim].  No transform.
+ * Errors: QMC_ERR_ARG/N/GENVEC/DIM/M/RANGE, QMC_ERR_CUDA. */
+int qmc_points(const qmc_rule *rule, uint64_t i_begin, uint64_t count, double *out, void *stream);
+
+/* Device scratch needed by qmc_sums for the i-range [i_begin, i_end) (per-tile partial
+ * sums; the tiling is fixed by the range, not by the device). */
+size_t qmc_sums_workspace_bytes(const qmc_rule *rule, int is_complex, uint64_t i_begin,
+                                uint64_t i_end);
+
+/* Per-shift sums S_k = sum_{i_begin <= i < i_end} g(x_{i,k}) (Eq. (lattice) before the 1/n).
+ * `f` holds device pointers.  sums (device) receives double-double pairs:
+ * sums[2k], sums[2k+1] = (hi, lo) of Re S_k, and for complex integrands
+ * sums[2m + 2k], sums[2m + 2k + 1] = (hi, lo) of Im S_k.  counters (device, may be NULL)
+ * receives [0] += samples that were NaN/Inf and [1] += complex sign-check failures.
+ * Errors: argument codes, QMC_ERR_WORKSPACE, QMC_ERR_CUDA. */
+int qmc_sums(const qmc_integrand *f, const qmc_rule *rule, uint64_t i_begin, uint64_t i_end,
+             void *workspace, size_t workspace_bytes, double *sums,
+             unsigned long long *counters, void *stream);
+
+/* Shift reduction (Eq. (lattice) and Eq. (lattice-error)) from device sums laid out as
+ * above over a lattice of size n: result (device) [4] = Qbar_re, sigma_re, Qbar_im,
+ * sigma_im, and Q (device, may be NULL) [m] or [2m] = per-shift Q^(k) re (then im).
+ * m >= 2.  Errors: QMC_ERR_ARG, QMC_ERR_M, QMC_ERR_CUDA. */
+int qmc_finalize(const double *sums, uint64_t m, uint64_t n, int is_complex, double *result,
+                 double *Q, void *stream);
+
+/* Raw samples f(x_i) on one shifted lattice (App. A.2 evaluate()): out (device) [count]
+ * (real) or [2*count] interleaved (complex), x_i = {i z/n + Delta} with shift (device)
+ * [dim] 53-bit integers; no transform, no fit. */
+int qmc_evaluate(const qmc_integrand *f, uint64_t n, const uint64_t *z, int dim,
+                 const uint64_t *shift, uint64_t i_begin, uint64_t count, double *out,
+                 void *stream);
+
+/* Per-dimension histogram of |f| over all n points of one shifted lattice (the data pass
+ * of the fit, Sec. 2.4): hist (device) [dim][bins] += |f(x_i)| at bin floor(x_ij * bins)
+ * (clamped to bins-1); hist is zeroed first.  workspace (device) must hold
+ * qmc_histogram_workspace_bytes(n, dim, bins) bytes (per-block partial histograms, summed
+ * in block order: the result is deterministic).  dim * bins <= 20480. */
+size_t qmc_histogram_workspace_bytes(uint64_t n, int dim, int bins);
+int qmc_histogram(const qmc_integrand *f, uint64_t n, const uint64_t *z, int dim,
+                  const uint64_t *shift, int bins, double *hist, void *workspace,
+                  size_t workspace_bytes, void *stream);
+
+/* ---- host entry points -------------------------------------------------------------- */
+
+/* Fit the PolySingular map (Eq. (ISfit), |a2|, |a3| form of App. A.5) per dimension to
+ * the inverse CDF taken from a host histogram hist[dim][bins]: data pairs
+ * (CDF(b/bins), b/bins) for every stepsize-th edge, Levenberg-Marquardt with
+ * a0 >= 1.001, a1 <= -0.001.  params (host) [dim][6]. */
+int qmc_fit_polysingular(const double *hist, int dim, int bins, const qmc_fit_opts *opts,
+                         double *params);
+
+/* Integrate with host buffers (the paper's integrate(), App. A.2).
+ *   f: host arrays.  table: host.  m: shifts (the paper's minm).
+ *   opts == NULL: fixed lattice (Sec. 3.3.2, Case 2): n = get_next_n(n_or_minn), one pass.
+ *   opts != NULL: adaptive (Sec. 3.3.1, Case 1): start at get_next_n(n_or_minn); while the
+ *     error goal (|E - I| <= max(epsabs, epsrel |I|), per component or by errormode) fails
+ *     and evaluations stay below maxeval, discard the result and take a larger table size;
+ *     past the largest size, double m.  The last result is returned.
+ *   fit: NULL or enabled == 0 for no variance reduction; else fit on a lattice of
+ *     >= evaluateminn points first and integrate the fitted, then periodized, integrand.
+ *   Shifts come from qmc_make_shifts(seed, m, dim).  Device memory is library-owned and
+ *   reused across calls on the same device.
+ * Returns QMC_OK, an error code, or QMC_ERR_NONFINITE when samples were NaN/Inf (out is
+ * filled, out->nonfinite counts them). */
+int qmc_integrate(const qmc_integrand *f, const qmc_genvec_table *table, uint64_t n_or_minn,
+                  uint64_t m, qmc_transform transform, const qmc_fit_opts *fit, uint64_t seed,
+                  const qmc_options *opts, void *stream, qmc_result *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QMC_GB300_H */

@@ -65,7 +65,7 @@ def lib():
         L.oracle_polysingular.argtypes = [P(dbl), dbl, P(dbl), P(dbl)]
         L.oracle_eval_g.argtypes = [P(_Integrand), i32, i32, i32, P(dbl), P(dbl), P(dbl), P(dbl)]
         L.oracle_shift_sums.argtypes = [P(_Integrand), i32, i32, i32, P(dbl), u64, P(u64), P(u64),
-                                        i32, u64, u64, P(dbl), P(dbl), i32]
+                                        i32, u64, u64, P(dbl), P(dbl), P(dbl), i32]
         L.oracle_shift_sums.restype = C.c_long
         L.oracle_evaluate.argtypes = [P(_Integrand), u64, P(u64), P(u64), u64, u64, P(dbl), P(dbl)]
         L.oracle_histogram.argtypes = [P(_Integrand), u64, P(u64), P(u64), i32, P(dbl)]
@@ -235,7 +235,8 @@ def eval_g(f: Integrand, transform, u, fitp=None) -> complex:
 def shift_sums(f: Integrand, transform, n: int, z, D, fitp=None, i0: int = 0,
                i1: int | None = None, nthreads: int | None = None):
     """Per-shift sums over i0 <= i < i1 as double-double: returns dict with
-    ``re`` (m, 2) [hi, lo], ``im`` (m, 2) or None, and ``signfail`` count."""
+    ``re`` (m, 2) [hi, lo], ``im`` (m, 2) or None, ``abs`` (m,) sum of |g| and the
+    ``signfail`` count."""
     s = f.struct()
     z = _u64(z)
     D = _u64(D)
@@ -246,13 +247,15 @@ def shift_sums(f: Integrand, transform, n: int, z, D, fitp=None, i0: int = 0,
     fp = None if fitp is None else _f64(fitp)
     re = np.zeros((m, 2))
     im = np.zeros((m, 2)) if f.is_complex else None
+    ab = np.zeros(m)
     k, r0, r1 = _tr(transform)
     fails = lib().oracle_shift_sums(C.byref(s), k, r0, r1,
                                     None if fp is None else _p(fp, C.c_double), n,
                                     _p(z, C.c_uint64), _p(D, C.c_uint64), m, i0, i1,
                                     _p(re, C.c_double),
-                                    None if im is None else _p(im, C.c_double), nthreads)
-    return {"re": re, "im": im, "signfail": int(fails)}
+                                    None if im is None else _p(im, C.c_double),
+                                    _p(ab, C.c_double), nthreads)
+    return {"re": re, "im": im, "abs": ab, "signfail": int(fails)}
 
 
 def shift_reduce(Q) -> tuple:
@@ -269,7 +272,7 @@ def integrate(f: Integrand, transform, n: int, z, D, fitp=None, nthreads=None):
     """Fixed-lattice estimate: per-shift Q^(k) = S_k / n, their mean and standard error."""
     r = shift_sums(f, transform, n, z, D, fitp=fitp, nthreads=nthreads)
     Qre = (r["re"][:, 0] + r["re"][:, 1]) / n
-    out = {"Q_re": Qre, "sums_re": r["re"], "signfail": r["signfail"]}
+    out = {"Q_re": Qre, "sums_re": r["re"], "signfail": r["signfail"], "A": r["abs"] / n}
     out["value_re"], out["error_re"] = shift_reduce(Qre)
     if r["im"] is not None:
         Qim = (r["im"][:, 0] + r["im"][:, 1]) / n

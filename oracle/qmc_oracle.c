@@ -438,22 +438,24 @@ static void dd_add_dd(dd *s, dd v) {
 #define OBLOCK 16384
 
 /* sums: [m][2] = (hi, lo) of the real part; sums_im likewise for complex integrands (may
- * be NULL for real).  The index range is split in fixed blocks of OBLOCK points whose
+ * be NULL for real); sums_abs (may be NULL): [m] sum of |g| (modulus), the scale against
+ * which agreement with other implementations is judged.  The index range is split in fixed blocks of OBLOCK points whose
  * double-double partials are combined in block order, so the result does not depend on
  * nthreads.  Returns the number of sign-check failures (complex family) or 0. */
 long oracle_shift_sums(const oracle_integrand *f, int tkind, int r0, int r1, const double *fitp,
                        uint64_t n, const uint64_t *z, const uint64_t *D, int m,
-                       uint64_t i0, uint64_t i1, double *sums, double *sums_im, int nthreads) {
+                       uint64_t i0, uint64_t i1, double *sums, double *sums_im, double *sums_abs,
+                       int nthreads) {
     int d = f->d;
     oracle_transform t = {tkind, r0, r1};
     uint64_t nblk = (i1 > i0) ? (i1 - i0 + OBLOCK - 1) / OBLOCK : 0;
-    dd *part = (dd *)calloc((size_t)(nblk ? nblk : 1) * m * 2, sizeof(dd));
+    dd *part = (dd *)calloc((size_t)(nblk ? nblk : 1) * m * 3, sizeof(dd));
     long fails = 0;
     (void)nthreads;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1) reduction(+ : fails)
     for (uint64_t b = 0; b < nblk; b++) {
         uint64_t lo = i0 + b * OBLOCK, hi = lo + OBLOCK < i1 ? lo + OBLOCK : i1;
-        dd *pr = part + b * m * 2, *pi = pr + m;
+        dd *pr = part + b * m * 3, *pi = pr + m, *pa = pi + m;
         double u[OMAXD];
         for (uint64_t i = lo; i < hi; i++) {
             for (int k = 0; k < m; k++) {
@@ -465,17 +467,20 @@ long oracle_shift_sums(const oracle_integrand *f, int tkind, int r0, int r1, con
                 fails += sf;
                 dd_add(&pr[k], re);
                 if (is_complex(f)) dd_add(&pi[k], im);
+                dd_add(&pa[k], is_complex(f) ? hypot(re, im) : fabs(re));
             }
         }
     }
     for (int k = 0; k < m; k++) {
-        dd sr = {0.0, 0.0}, si = {0.0, 0.0};
+        dd sr = {0.0, 0.0}, si = {0.0, 0.0}, sa = {0.0, 0.0};
         for (uint64_t b = 0; b < nblk; b++) {
-            dd_add_dd(&sr, part[b * m * 2 + k]);
-            dd_add_dd(&si, part[b * m * 2 + m + k]);
+            dd_add_dd(&sr, part[b * m * 3 + k]);
+            dd_add_dd(&si, part[b * m * 3 + m + k]);
+            dd_add_dd(&sa, part[b * m * 3 + 2 * m + k]);
         }
         sums[2 * k] = sr.hi; sums[2 * k + 1] = sr.lo;
         if (sums_im) { sums_im[2 * k] = si.hi; sums_im[2 * k + 1] = si.lo; }
+        if (sums_abs) sums_abs[k] = sa.hi + sa.lo;
     }
     free(part);
     return fails;

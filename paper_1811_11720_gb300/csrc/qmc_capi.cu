@@ -1,0 +1,422 @@
+// qmc_capi.cu -- the C ABI declared in include/qmc_gb300.h.
+//
+// Host responsibilities: argument validation, lattice constants (Fz, remz) in exact
+// 128-bit host arithmetic, SplitMix64 shifts, Korobov/Sidi coefficient tables, the tile
+// geometry, kernel dispatch, and the host-buffer integrate() with its adaptive loop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "qmc_gb300.h"
+#include "qmc_internal.h"
+
+using namespace qmc;
+
+namespace {
+
+typedef unsigned __int128 u128_t;
+
+const uint64_t kNMax = (uint64_t)1 << 63;
+
+uint64_t gcd_u64(uint64_t a, uint64_t b) {
+    while (b) {
+        uint64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// floor(z 2^128 / n) and z 2^128 mod n for z < n, by two 128/64 divisions.
+DimConst dim_const(uint64_t z, uint64_t n) {
+    u128_t a = (u128_t)z << 64;
+    uint64_t q1 = (uint64_t)(a / n);
+    uint64_t r1 = (uint64_t)(a % n);
+    u128_t b = (u128_t)r1 << 64;
+    uint64_t q0 = (uint64_t)(b / n);
+    uint64_t r0 = (uint64_t)(b % n);
+    return DimConst{q1, q0, r0};
+}
+
+double binom(int a, int b) {
+    double r = 1.0;
+    for (int i = 1; i <= b; ++i) r = r * (a - b + i) / i;
+    return r;
+}
+
+int check_transform(const qmc_transform &t) {
+    switch (t.kind) {
+    case QMC_T_NONE:
+    case QMC_T_BAKER: return QMC_OK;
+    case QMC_T_KOROBOV:
+        return (t.r0 >= 0 && t.r1 >= 0 && t.r0 <= kMaxKorobov && t.r1 <= kMaxKorobov) ? QMC_OK : QMC_ERR_TRANSFORM;
+    case QMC_T_SIDI: return (t.r0 >= 1 && t.r0 <= kMaxSidi) ? QMC_OK : QMC_ERR_TRANSFORM;
+    default: return QMC_ERR_TRANSFORM;
+    }
+}
+
+TransformParams make_transform(const qmc_transform &t) {
+    TransformParams tp;
+    std::memset(&tp, 0, sizeof(tp));
+    tp.kind = t.kind;
+    tp.r0 = t.r0;
+    tp.r1 = t.r1;
+    if (t.kind == QMC_T_KOROBOV) {
+        const int r0 = t.r0, r1 = t.r1;
+        tp.C = (r0 + r1 + 1) * binom(r0 + r1, r0);
+        tp.deg = std::max(r0, r1);
+        // phi(u) = u^(r0+1) sum_k A_k u^k with A_k = C (-1)^k C(r1,k)/(r0+k+1): the
+        // binomial expansion of (1-t)^r1 integrated term by term (Eq. (korobov)).
+        for (int k = 0; k <= r1; ++k) tp.A[k] = tp.C * ((k & 1) ? -1.0 : 1.0) * binom(r1, k) / (r0 + k + 1);
+        for (int k = 0; k <= r0; ++k) tp.B[k] = tp.C * ((k & 1) ? -1.0 : 1.0) * binom(r0, k) / (r1 + k + 1);
+    } else if (t.kind == QMC_T_SIDI) {
+        const int r = t.r0;
+        tp.r1 = r;
+        // c_r = (pi / 2^r) Gamma(r+1) / Gamma((r+1)/2)^2 (Eq. (sidi))
+        double g = std::tgamma((r + 1.0) / 2.0);
+        tp.C = M_PI / std::ldexp(1.0, r) * std::tgamma(r + 1.0) / (g * g);
+        // I_r = -s^(r-1) c/(r pi) + (r-1)/r I_(r-2): a_q and the trailing factor
+        double carry = 1.0;
+        int nq = r / 2;
+        for (int q = 0; q < nq; ++q) {
+            int rr = r - 2 * q;
+            tp.sidi_c[q] = carry / rr;
+            carry *= (double)(rr - 1) / rr;
+        }
+        if (nq == 0) tp.sidi_c[0] = 0.0;
+        tp.sidi_c[kMaxSidi] = carry;
+    }
+    return tp;
+}
+
+bool is_complex_family(int fam) { return fam == QMC_FEYNMAN; }
+
+bool family_known(int fam) {
+    switch (fam) {
+    case QMC_GENZ_OSCILLATORY: case QMC_GENZ_PRODUCT_PEAK: case QMC_GENZ_CORNER_PEAK:
+    case QMC_GENZ_GAUSSIAN: case QMC_GENZ_C0: case QMC_GENZ_DISCONTINUOUS: case QMC_MONOMIAL:
+    case QMC_TRIG: case QMC_SECTOR: case QMC_FEYNMAN: return true;
+    default: return false;
+    }
+}
+
+int check_integrand_shape(const qmc_integrand *f) {
+    if (!f) return QMC_ERR_ARG;
+    if (!family_known(f->family)) return QMC_ERR_INTEGRAND;
+    if (f->dim < 1 || f->dim > QMC_MAX_DIM) return QMC_ERR_DIM;
+    switch (f->family) {
+    case QMC_MONOMIAL: return QMC_OK;
+    case QMC_TRIG: return (f->c && f->w && f->h) ? QMC_OK : QMC_ERR_INTEGRAND;
+    case QMC_SECTOR:
+    case QMC_FEYNMAN:
+        if (f->nu < 1 || f->nf < 1 || f->nu > QMC_MAX_TERMS || f->nf > QMC_MAX_TERMS) return QMC_ERR_INTEGRAND;
+        return (f->ucoef && f->fcoef && f->uexp && f->fexp) ? QMC_OK : QMC_ERR_INTEGRAND;
+    case QMC_GENZ_OSCILLATORY:
+        return (f->c && f->w) ? QMC_OK : QMC_ERR_INTEGRAND;
+    default:
+        return (f->c && f->w) ? QMC_OK : QMC_ERR_INTEGRAND;
+    }
+}
+
+int check_rule(const qmc_rule *r) {
+    if (!r) return QMC_ERR_ARG;
+    if (r->dim < 1 || r->dim > QMC_MAX_DIM) return QMC_ERR_DIM;
+    if (r->n < 2 || r->n >= kNMax) return QMC_ERR_N;
+    if (r->m < 1 || r->m > QMC_MAX_SHIFTS) return QMC_ERR_M;
+    if (!r->shifts) return QMC_ERR_ARG;
+    for (int j = 0; j < r->dim; ++j) {
+        uint64_t z = r->z[j] % r->n;
+        if (z == 0 || gcd_u64(z, r->n) != 1) return QMC_ERR_GENVEC;
+    }
+    return check_transform(r->transform);
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? QMC_OK : QMC_ERR_CUDA; }
+
+int device_ok() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return QMC_ERR_NO_DEVICE;
+    int major = 0, minor = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
+        return QMC_ERR_NO_DEVICE;
+    return (major == 10 && minor == 3) ? QMC_OK : QMC_ERR_NO_DEVICE;
+}
+
+// Tile geometry, a function of (range, m) only.
+struct Geometry {
+    int spb;          // streams per block
+    int threads;      // spb * mg
+    uint32_t L;       // points per stream per tile
+    uint64_t tiles;
+};
+
+constexpr int kMaxShiftGroup = kSumsThreads;   // shifts per launch (block holds spb * m threads)
+constexpr uint64_t kTargetTiles = 4096;
+
+Geometry geometry(uint64_t range, int mg) {
+    Geometry g;
+    g.spb = std::max(1, kSumsThreads / mg);
+    g.threads = g.spb * mg;
+    uint64_t per = (range + (uint64_t)g.spb * kTargetTiles - 1) / ((uint64_t)g.spb * kTargetTiles);
+    per = std::max<uint64_t>(32, std::min<uint64_t>(8192, per));
+    g.L = (uint32_t)per;
+    uint64_t ptile = (uint64_t)g.spb * g.L;
+    g.tiles = range ? (range + ptile - 1) / ptile : 0;
+    return g;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+void fill_integrand(SumsParams &p, const qmc_integrand *f) {
+    p.family = f->family;
+    p.c = f->c;
+    p.w = f->w;
+    p.h = f->h;
+    p.nu = f->nu;
+    p.nf = f->nf;
+    p.ucoef = f->ucoef;
+    p.fcoef = f->fcoef;
+    p.uexp = f->uexp;
+    p.fexp = f->fexp;
+    p.pa = f->pa;
+    p.pb = f->pb;
+    p.lam = f->lambda;
+}
+
+cudaError_t launch_sums_any(int family, int tkind, dim3 g, dim3 b, cudaStream_t s, const SumsParams &p) {
+    switch (family) {
+    case QMC_GENZ_OSCILLATORY: case QMC_GENZ_PRODUCT_PEAK: case QMC_GENZ_CORNER_PEAK: case QMC_GENZ_GAUSSIAN:
+        return launch_sums_genz(family, tkind, g, b, s, p);
+    case QMC_GENZ_C0: case QMC_GENZ_DISCONTINUOUS: case QMC_MONOMIAL: case QMC_TRIG:
+        return launch_sums_other(family, tkind, g, b, s, p);
+    case QMC_SECTOR: case QMC_FEYNMAN:
+        return launch_sums_poly(family, tkind, g, b, s, p);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+uint64_t splitmix64_output(uint64_t seed, uint64_t t) {
+    // SplitMix64 (Steele, Lea, Flood 2014): state advances by the golden-ratio increment,
+    // the output is the state passed through the published finaliser.
+    uint64_t x = seed + (t + 1) * 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+
+}  // namespace
+
+// ======================================================================================
+extern "C" {
+
+const char *qmc_strerror(int code) {
+    switch (code) {
+    case QMC_OK: return "ok";
+    case QMC_ERR_ARG: return "invalid argument";
+    case QMC_ERR_DIM: return "dimension out of range";
+    case QMC_ERR_N: return "lattice size out of range or not in the table";
+    case QMC_ERR_GENVEC: return "generating vector component not coprime to n";
+    case QMC_ERR_M: return "number of shifts out of range (m >= 2 needed for an error)";
+    case QMC_ERR_FIT_PARAMS: return "PolySingular parameters violate a0 >= 1.001, a1 <= -0.001";
+    case QMC_ERR_INTEGRAND: return "unknown integrand family or bad coefficient arrays";
+    case QMC_ERR_TRANSFORM: return "unknown transform or order out of range";
+    case QMC_ERR_CUDA: return "CUDA runtime error";
+    case QMC_ERR_WORKSPACE: return "workspace too small";
+    case QMC_ERR_NONFINITE: return "integrand produced NaN or Inf";
+    case QMC_ERR_RANGE: return "index range or bin count out of range";
+    case QMC_ERR_NO_DEVICE: return "no sm_103 CUDA device";
+    default: return "unknown error";
+    }
+}
+
+int qmc_abi_version(void) { return QMC_ABI_VERSION; }
+
+int qmc_get_next_n(const qmc_genvec_table *t, uint64_t preferred, uint64_t *n_out) {
+    if (!t || !t->n || !n_out || t->count < 1) return QMC_ERR_ARG;
+    for (int c = 0; c < t->count; ++c)
+        if (t->n[c] >= preferred) {
+            *n_out = t->n[c];
+            return QMC_OK;
+        }
+    return QMC_ERR_N;
+}
+
+int qmc_make_shifts(uint64_t seed, uint64_t m, int dim, uint64_t *D_out) {
+    if (!D_out) return QMC_ERR_ARG;
+    if (dim < 1 || dim > QMC_MAX_DIM) return QMC_ERR_DIM;
+    if (m < 1 || m > QMC_MAX_SHIFTS) return QMC_ERR_M;
+    for (uint64_t k = 0; k < m; ++k)
+        for (int j = 0; j < dim; ++j)
+            D_out[k * dim + j] = splitmix64_output(seed, k * (uint64_t)dim + j) >> 11;
+    return QMC_OK;
+}
+
+int qmc_points(const qmc_rule *rule, uint64_t i_begin, uint64_t count, double *out, void *stream) {
+    int st = check_rule(rule);
+    if (st) return st;
+    if (!out) return QMC_ERR_ARG;
+    if (i_begin > rule->n || count > rule->n - i_begin) return QMC_ERR_RANGE;
+    if ((st = device_ok())) return st;
+    PointsParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.n = rule->n;
+    p.i_begin = i_begin;
+    p.count = count;
+    p.d = rule->dim;
+    p.m = (int)rule->m;
+    p.L = 64;
+    for (int j = 0; j < rule->dim; ++j) p.dc[j] = dim_const(rule->z[j] % rule->n, rule->n);
+    p.shifts = rule->shifts;
+    p.out = out;
+    return cuda_status(launch_points(p, (cudaStream_t)stream));
+}
+
+size_t qmc_sums_workspace_bytes(const qmc_rule *rule, int is_complex, uint64_t i_begin,
+                                uint64_t i_end) {
+    if (!rule || i_end <= i_begin || rule->m < 1) return 0;
+    size_t total = 0;
+    for (uint64_t k0 = 0; k0 < rule->m; k0 += kMaxShiftGroup) {
+        int mg = (int)std::min<uint64_t>(kMaxShiftGroup, rule->m - k0);
+        Geometry g = geometry(i_end - i_begin, mg);
+        total += align256(g.tiles * (uint64_t)mg * 2 * sizeof(double) * (is_complex ? 2 : 1));
+    }
+    return total;
+}
+
+int qmc_sums(const qmc_integrand *f, const qmc_rule *rule, uint64_t i_begin, uint64_t i_end,
+             void *workspace, size_t workspace_bytes, double *sums, unsigned long long *counters,
+             void *stream) {
+    int st = check_integrand_shape(f);
+    if (st) return st;
+    if ((st = check_rule(rule))) return st;
+    if (f->dim != rule->dim) return QMC_ERR_DIM;
+    if (!sums || !workspace) return QMC_ERR_ARG;
+    if (i_end <= i_begin || i_end > rule->n) return QMC_ERR_RANGE;
+    const int cplx = is_complex_family(f->family);
+    if (workspace_bytes < qmc_sums_workspace_bytes(rule, cplx, i_begin, i_end)) return QMC_ERR_WORKSPACE;
+    if ((st = device_ok())) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    SumsParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.n = rule->n;
+    p.i_begin = i_begin;
+    p.i_end = i_end;
+    p.d = rule->dim;
+    for (int j = 0; j < rule->dim; ++j) p.dc[j] = dim_const(rule->z[j] % rule->n, rule->n);
+    p.t = make_transform(rule->transform);
+    p.fit = rule->fit;
+    fill_integrand(p, f);
+    p.counters = counters;
+
+    char *ws = (char *)workspace;
+    const uint64_t m = rule->m;
+    for (uint64_t k0 = 0; k0 < m; k0 += kMaxShiftGroup) {
+        const int mg = (int)std::min<uint64_t>(kMaxShiftGroup, m - k0);
+        Geometry g = geometry(i_end - i_begin, mg);
+        p.m = mg;
+        p.spb = g.spb;
+        p.L = g.L;
+        p.tiles = g.tiles;
+        p.shifts = rule->shifts + k0 * rule->dim;
+        p.partials = (double *)ws;
+        cudaError_t e = launch_sums_any(f->family, rule->transform.kind, dim3((unsigned)g.tiles),
+                                        dim3(g.threads), s, p);
+        if (e != cudaSuccess) return QMC_ERR_CUDA;
+        // sums layout: re pairs for all m, then im pairs for all m; group k0 writes its slice
+        double *grp = sums + 2 * k0;
+        if (!cplx) {
+            e = launch_reduce_tiles(p.partials, g.tiles, mg, 0, grp, s);
+        } else {
+            // the reduce kernel writes [re (2 mg)] [im (2 mg)] contiguously; reduce each
+            // component separately so that im lands at sums + 2m + 2 k0
+            e = launch_reduce_tiles(p.partials, g.tiles, mg, 0, grp, s);
+            if (e == cudaSuccess)
+                e = launch_reduce_tiles(p.partials + 2 * g.tiles * (uint64_t)mg, g.tiles, mg, 0,
+                                        sums + 2 * m + 2 * k0, s);
+        }
+        if (e != cudaSuccess) return QMC_ERR_CUDA;
+        ws += align256(g.tiles * (uint64_t)mg * 2 * sizeof(double) * (cplx ? 2 : 1));
+    }
+    return QMC_OK;
+}
+
+int qmc_finalize(const double *sums, uint64_t m, uint64_t n, int is_complex, double *result,
+                 double *Q, void *stream) {
+    if (!sums || !result) return QMC_ERR_ARG;
+    if (m < 2 || m > QMC_MAX_SHIFTS) return QMC_ERR_M;
+    if (n < 1) return QMC_ERR_N;
+    int st = device_ok();
+    if (st) return st;
+    return cuda_status(launch_finalize(sums, (int)m, n, is_complex ? 1 : 0, result, Q, (cudaStream_t)stream));
+}
+
+int qmc_evaluate(const qmc_integrand *f, uint64_t n, const uint64_t *z, int dim,
+                 const uint64_t *shift, uint64_t i_begin, uint64_t count, double *out, void *stream) {
+    int st = check_integrand_shape(f);
+    if (st) return st;
+    if (!z || !shift || !out) return QMC_ERR_ARG;
+    if (dim != f->dim) return QMC_ERR_DIM;
+    if (n < 2 || n >= kNMax) return QMC_ERR_N;
+    if (i_begin > n || count > n - i_begin) return QMC_ERR_RANGE;
+    for (int j = 0; j < dim; ++j)
+        if (z[j] % n == 0 || gcd_u64(z[j] % n, n) != 1) return QMC_ERR_GENVEC;
+    if ((st = device_ok())) return st;
+    if (count == 0) return QMC_OK;
+    SumsParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.n = n;
+    p.i_begin = i_begin;
+    p.i_end = i_begin + count;
+    p.d = dim;
+    p.m = 1;
+    for (int j = 0; j < dim; ++j) p.dc[j] = dim_const(z[j] % n, n);
+    p.shifts = shift;
+    fill_integrand(p, f);
+    return cuda_status(launch_evaluate(p, out, (cudaStream_t)stream));
+}
+
+static uint32_t hist_blocks(uint64_t n) {
+    uint64_t b = (n + 4095) / 4096;
+    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(b, 1024));
+}
+
+size_t qmc_histogram_workspace_bytes(uint64_t n, int dim, int bins) {
+    if (dim < 1 || dim > QMC_MAX_DIM || bins < 1 || n < 1) return 0;
+    return (size_t)hist_blocks(n) * dim * bins * sizeof(double);
+}
+
+int qmc_histogram(const qmc_integrand *f, uint64_t n, const uint64_t *z, int dim,
+                  const uint64_t *shift, int bins, double *hist, void *workspace,
+                  size_t workspace_bytes, void *stream) {
+    int st = check_integrand_shape(f);
+    if (st) return st;
+    if (!z || !shift || !hist || !workspace) return QMC_ERR_ARG;
+    if (dim != f->dim) return QMC_ERR_DIM;
+    if (n < 2 || n >= kNMax) return QMC_ERR_N;
+    if (bins < 1 || (size_t)dim * bins > 20480) return QMC_ERR_RANGE;
+    for (int j = 0; j < dim; ++j)
+        if (z[j] % n == 0 || gcd_u64(z[j] % n, n) != 1) return QMC_ERR_GENVEC;
+    uint32_t nb = hist_blocks(n);
+    if (workspace_bytes < (size_t)nb * dim * bins * sizeof(double)) return QMC_ERR_WORKSPACE;
+    if ((st = device_ok())) return st;
+    SumsParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.n = n;
+    p.i_begin = 0;
+    p.i_end = n;
+    p.d = dim;
+    p.m = 1;
+    for (int j = 0; j < dim; ++j) p.dc[j] = dim_const(z[j] % n, n);
+    p.shifts = shift;
+    fill_integrand(p, f);
+    return cuda_status(launch_histogram(p, bins, hist, (double *)workspace, nb, (cudaStream_t)stream));
+}
+
+}  // extern "C"

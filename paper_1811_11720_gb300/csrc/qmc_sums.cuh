@@ -1,0 +1,148 @@
+// qmc_sums.cuh -- the persistent lattice-sum kernel (Eq. (lattice)).
+//
+// Work decomposition.  The i-range [i_begin, i_end) is cut into tiles of spb * L points;
+// a block of spb * m threads owns one tile at a time (tiles are dealt round-robin to a
+// persistent grid).  Thread (s, k) evaluates shift k on the L consecutive points of
+// stream s, so the 32 lanes of a warp are 32 shifts of the same points when m = 32: the
+// integer lattice state is identical across the warp and the FP64 instruction stream is
+// uniform.  Each thread accumulates its L samples in FP64; the tile's per-shift partial is
+// the Neumaier-compensated sum over its spb streams in fixed order, written to
+// partials[tile][k].  Tiles depend only on the i-range, so the result is bit-identical for
+// any grid size, and sharding on tile boundaries reproduces the same partials.
+#pragma once
+#include <cstdint>
+
+#include "qmc_integrands.cuh"
+#include "qmc_transforms.cuh"
+
+namespace qmc {
+
+constexpr uint64_t kInner = 64;   // samples per inner accumulation block (power of two)
+
+__device__ __forceinline__ bool not_finite(double x) {
+    return ((unsigned long long)__double_as_longlong(x) & 0x7FF0000000000000ull) ==
+           0x7FF0000000000000ull;
+}
+
+// Neumaier: add v to (s, c).
+__device__ __forceinline__ void neumaier_add(double &s, double &c, double v) {
+    double t = s + v;
+    if (fabs(s) >= fabs(v)) c += (s - t) + v;
+    else c += (v - t) + s;
+    s = t;
+}
+
+template <int FAM, int TK>
+__global__ void __launch_bounds__(kSumsThreads) sums_kernel(const __grid_constant__ SumsParams p) {
+    __shared__ FamilyShared fsh;
+    __shared__ double s_fit[kMaxDim * kFitStride];
+    __shared__ double s_red[2 * kSumsThreads];
+
+    const int tid = threadIdx.x;
+    stage_family<FAM>(p, fsh);
+    const bool use_fit = p.fit != nullptr;
+    if (use_fit && tid < p.d) {
+        const double *a = p.fit + 6 * tid;
+        double a2 = fabs(a[2]), a3 = fabs(a[3]);
+        double *o = s_fit + kFitStride * tid;
+        o[0] = a[0];
+        o[1] = a[1];
+        o[2] = a2 * (a[0] - 1.0);
+        o[3] = a3 * (a[1] - 1.0);
+        o[4] = a[4];
+        o[5] = a[5];
+        o[6] = 1.0 - a2 - a3 - a[4] - a[5];
+        o[7] = o[2] * a[0];
+        o[8] = o[3] * a[1];
+    }
+    __syncthreads();
+
+    const int m = p.m, d = p.d;
+    const int k = tid % m;
+    const int s_local = tid / m;
+    const bool active = s_local < p.spb;
+    const uint64_t n = p.n;
+    double cd = 1.0;  // Korobov C^d
+    if constexpr (TK == QMC_T_KOROBOV) cd = ipow_u(p.t.C, d);
+
+    // per-thread state lives in local memory (L1): the dimension loop is not unrolled,
+    // which keeps the register count low; the FP64 pipe, not L1, bounds the kernel
+    uint64_t dsh[kMaxDim];
+#pragma unroll 1
+    for (int j = 0; j < d; ++j) dsh[j] = active ? (p.shifts[(size_t)k * d + j] << 11) : 0ull;
+
+    unsigned long long nonfinite = 0, signfail = 0;
+    const uint64_t ptile = (uint64_t)p.spb * p.L;
+
+    for (uint64_t tile = blockIdx.x; tile < p.tiles; tile += gridDim.x) {
+        const uint64_t i0 = p.i_begin + tile * ptile + (uint64_t)s_local * p.L;
+        uint64_t cnt = 0;
+        if (active && i0 < p.i_end) cnt = (p.i_end - i0 < p.L) ? (p.i_end - i0) : p.L;
+        // two-level FP64 accumulation: blocks of kInner samples, then the block sums
+        // (rounding error ~ (kInner + L/kInner) ulp instead of L ulp)
+        double acc_re = 0.0, acc_im = 0.0, in_re = 0.0, in_im = 0.0;
+        if (cnt) {
+            uint64_t fhi[kMaxDim], flo[kMaxDim], rem[kMaxDim];
+#pragma unroll 1
+            for (int j = 0; j < d; ++j) lattice_state_at(i0, p.dc[j], n, fhi[j], flo[j], rem[j]);
+#pragma unroll 1
+            for (uint64_t t = 0; t < cnt; ++t) {
+                Weight W{1.0, 1.0, 1.0};
+                FamilyAcc<FAM> fa;
+                fa.init(fsh);
+#pragma unroll 1
+                for (int j = 0; j < d; ++j) {
+                    double u = fixed_to_double(fhi[j] + dsh[j], flo[j], rem[j], n);
+                    double x = apply_transform<TK>(u, p.t, W);
+                    if (use_fit) x = apply_fit(x, s_fit + kFitStride * j, W.w);
+                    fa.add(j, x, fsh);
+                    lattice_step(p.dc[j], n, fhi[j], flo[j], rem[j]);
+                }
+                double wt = weight_finish<TK>(W, p.t, cd);
+                double g_re, g_im;
+                fa.finish(d, fsh, g_re, g_im, signfail);
+                g_re *= wt;
+                if constexpr (FamilyAcc<FAM>::kComplex) g_im *= wt;
+                if (not_finite(g_re) || (FamilyAcc<FAM>::kComplex && not_finite(g_im))) ++nonfinite;
+                in_re += g_re;
+                if constexpr (FamilyAcc<FAM>::kComplex) in_im += g_im;
+                if ((t & (kInner - 1)) == kInner - 1) {
+                    acc_re += in_re;
+                    in_re = 0.0;
+                    if constexpr (FamilyAcc<FAM>::kComplex) {
+                        acc_im += in_im;
+                        in_im = 0.0;
+                    }
+                }
+            }
+            acc_re += in_re;
+            if constexpr (FamilyAcc<FAM>::kComplex) acc_im += in_im;
+        }
+        // per-shift tile partial: fixed-order compensated sum over the block's streams
+        s_red[tid] = acc_re;
+        if constexpr (FamilyAcc<FAM>::kComplex) s_red[kSumsThreads + tid] = acc_im;
+        __syncthreads();
+        if (s_local == 0 && active) {
+            double sr = 0.0, cr = 0.0, si = 0.0, ci = 0.0;
+            for (int s = 0; s < p.spb; ++s) {
+                neumaier_add(sr, cr, s_red[s * m + k]);
+                if constexpr (FamilyAcc<FAM>::kComplex) neumaier_add(si, ci, s_red[kSumsThreads + s * m + k]);
+            }
+            double *out = p.partials + 2 * (tile * (uint64_t)m + k);
+            out[0] = sr;
+            out[1] = cr;
+            if constexpr (FamilyAcc<FAM>::kComplex) {
+                double *oi = p.partials + 2 * (p.tiles * (uint64_t)m) + 2 * (tile * (uint64_t)m + k);
+                oi[0] = si;
+                oi[1] = ci;
+            }
+        }
+        __syncthreads();
+    }
+    if (p.counters && (nonfinite | signfail)) {
+        if (nonfinite) atomicAdd(p.counters, nonfinite);
+        if (signfail) atomicAdd(p.counters + 1, signfail);
+    }
+}
+
+}  // namespace qmc

@@ -1,0 +1,95 @@
+// qmc_transforms.cuh -- periodizing transforms (Sec. 2.3) and the PolySingular
+// variance-reduction map (Sec. 2.4, Eq. (ISfit)) as device functions.
+//
+// FP64 is the bottleneck on GB300, so every step that is exact in integer arithmetic is
+// done on the integer pipe: comparisons of non-negative doubles are integer comparisons
+// of their bit patterns, 1 - u for u >= 1/2 (exact by Sterbenz' lemma) and multiplication
+// by 2 are bit manipulations.
+#pragma once
+#include <cstdint>
+
+#include "qmc_fp.cuh"
+#include "qmc_params.cuh"
+
+namespace qmc {
+
+// Per-evaluation weight accumulator.  For Korobov the weight prod_j C u_j^r0 (1-u_j)^r1
+// is kept as two running products, prod u_j and prod (1-u_j), raised to r0 and r1 once
+// per evaluation (C^d is folded into the final factor).
+struct Weight {
+    double wu, w1, w;   // prod u, prod (1-u), other factors (fit Jacobian, Sidi)
+};
+
+template <int TK>
+__device__ __forceinline__ double apply_transform(double u, const TransformParams &t, Weight &W) {
+    if constexpr (TK == QMC_T_NONE) {
+        return u;
+    } else if constexpr (TK == QMC_T_BAKER) {
+        // phi(u) = 2u for u <= 1/2, 2 - 2u = 2 (1 - u) otherwise (Eq. (baker)); weight 1.
+        return twice(le_half(u) ? u : one_minus_upper(u));
+    } else if constexpr (TK == QMC_T_KOROBOV) {
+        const bool lo = le_half(u);
+        const double w1 = 1.0 - u;           // exact for u >= 1/2
+        const double v = lo ? u : w1;
+        const int e = lo ? t.r0 + 1 : t.r1 + 1;
+        double pw = ipow_u(v, e);
+        double P = lo ? t.A[t.deg] : t.B[t.deg];
+#pragma unroll 1
+        for (int q = t.deg - 1; q >= 0; --q) P = fma(P, v, lo ? t.A[q] : t.B[q]);
+        const double ph = pw * P;
+        W.wu *= u;
+        W.w1 *= w1;
+        return lo ? ph : 1.0 - ph;
+    } else {  // QMC_T_SIDI
+        // phi = cr I_r(u), I_r = base I_(r mod 2) - (cos(pi u)/pi) sum_q a_q sin^(r-1-2q)
+        double s, c;
+        sincospi(u, &s, &c);
+        const int r = t.r0;
+        const double s2 = s * s;
+        // sum_{q < nq} a_q s^(r-1-2q), nq = floor(r/2): Horner in s^2 on a_0..a_(nq-1)
+        // (sidi_c[q] = a_q, zero when nq = 0), then one factor s (r even: powers
+        // r-1, ..., 1) or s^2 (r odd: powers r-1, ..., 2).
+        double poly = t.sidi_c[0];
+        const int nq = r / 2;
+#pragma unroll 1
+        for (int q = 1; q < nq; ++q) poly = fma(poly, s2, t.sidi_c[q]);
+        poly *= (r & 1) ? s2 : s;
+        double base = (r & 1) ? (1.0 - c) * 0.31830988618379067154 : u;
+        double I = t.sidi_c[kMaxSidi] * base - c * 0.31830988618379067154 * poly;
+        double sr = ipow_u(s, r);
+        W.w *= t.C * sr;
+        return t.C * I;
+    }
+}
+
+template <int TK>
+__device__ __forceinline__ double weight_finish(const Weight &W, const TransformParams &t,
+                                                double cd) {
+    if constexpr (TK == QMC_T_KOROBOV) {
+        return cd * ipow_u(W.wu, t.r0) * ipow_u(W.w1, t.r1) * W.w;
+    } else {
+        return W.w;
+    }
+}
+
+// PolySingular map p(x) and p'(x) (Eq. (ISfit) with |a2|, |a3| as in App. A.5).  fp holds
+// per-dimension constants prepared in shared memory:
+//   [0] a0, [1] a1, [2] |a2| (a0 - 1), [3] |a3| (a1 - 1), [4] a4, [5] a5,
+//   [6] a6 = 1 - |a2| - |a3| - a4 - a5, [7] |a2| (a0 - 1) a0, [8] |a3| (a1 - 1) a1.
+constexpr int kFitStride = 9;
+
+__device__ __forceinline__ double apply_fit(double x, const double *fp, double &jac) {
+    const double d0 = fp[0] - x;
+    const double d1 = fp[1] - x;
+    const double inv = 1.0 / (d0 * d1);
+    const double r0 = d1 * inv;   // 1 / (a0 - x)
+    const double r1 = d0 * inv;   // 1 / (a1 - x)
+    const double poly = fma(fma(fp[6], x, fp[5]), x, fp[4]);
+    const double p = x * fma(fp[2], r0, fma(fp[3], r1, poly));
+    const double dpoly = fma(fma(3.0 * fp[6], x, 2.0 * fp[5]), x, fp[4]);
+    const double dp = fma(fp[7] * r0, r0, fma(fp[8] * r1, r1, dpoly));
+    jac *= dp;
+    return p;
+}
+
+}  // namespace qmc

@@ -1,0 +1,369 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on identical seeded
+inputs.  Points are compared bit for bit; per-shift sums, the mean and the error within
+1e-12 of the mean |g| (the oracle's double-double sum of |g| / n), the bound derived in
+the design notes from the kernel's FP64 arithmetic (a few ulp per sample, two-level
+summation) with three orders of magnitude of margin."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from oracle import closed_forms as CF
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    import paper_1811_11720_gb300 as q
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test run without a CUDA device")
+    from paper_1811_11720_gb300 import build
+    build.build()
+    q.lib()
+    dev = torch.device("cuda:0")
+    return q, torch, dev, q.GenvecTable.load()
+
+
+def _dev_shifts(torch, D, dev):
+    return torch.from_numpy(np.ascontiguousarray(D).astype(np.int64)).to(dev)
+
+
+def _gpu_sums(env, f, n, z, D, transform, fitp=None, i0=0, i1=None):
+    q, torch, dev, _ = env
+    Dd = _dev_shifts(torch, D, dev)
+    fd = None if fitp is None else torch.from_numpy(np.ascontiguousarray(fitp)).to(dev)
+    res, sums, cnt = q.integrate_device(f, n, z, Dd, transform, fd, i0, n if i1 is None else i1)
+    torch.cuda.synchronize()
+    m = D.shape[0]
+    s = sums.cpu().numpy()
+    return res.cpu().numpy(), s[: 2 * m].reshape(m, 2), s[2 * m: 4 * m].reshape(m, 2), cnt.cpu().numpy()
+
+
+def _compare(gre, gim, o, n, is_complex=False, tol=TOL):
+    A = o["abs"] / n
+    Qg = (gre[:, 0] + gre[:, 1]) / n
+    Qo = (o["re"][:, 0] + o["re"][:, 1]) / n
+    assert np.all(np.abs(Qg - Qo) <= tol * A), np.max(np.abs(Qg - Qo) / A)
+    if is_complex:
+        Qgi = (gim[:, 0] + gim[:, 1]) / n
+        Qoi = (o["im"][:, 0] + o["im"][:, 1]) / n
+        assert np.all(np.abs(Qgi - Qoi) <= tol * A), np.max(np.abs(Qgi - Qoi) / A)
+    return Qg, Qo, A
+
+
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [7, 11, 55, 1021, 108863, 1024565021, 2147483647,
+                               1099511627791, 2305843009213693951])
+def test_points_bit_exact(env, n):
+    q, torch, dev, tab = env
+    rng = np.random.default_rng(n % 1000003)
+    d = 5
+    if n in tab:
+        z = [int(v) for v in tab.z_for(n)[:d]]
+    else:
+        z = []
+        while len(z) < d:
+            c = int(rng.integers(1, n - 1))
+            if np.gcd(c, n) == 1:
+                z.append(c)
+    m = 3
+    D = O.shifts(n & 0xFFFF, m, d)
+    D[0, 0] = 0          # a zero shift
+    Dd = _dev_shifts(torch, D, dev)
+    r = q.rule(n, z, Dd)
+    for i0, cnt in [(0, min(n, 300)), (max(0, n - 77), min(n, 77)), (n // 3, min(n - n // 3, 129))]:
+        out = torch.empty(cnt * m * d, dtype=torch.float64, device=dev)
+        q.points(r, i0, cnt, out)
+        got = out.cpu().numpy().view(np.uint64)
+        ref = O.points(n, z, D, i0, cnt).reshape(-1).view(np.uint64)
+        assert np.array_equal(got, ref), (n, i0)
+
+
+def test_points_smallest_fractions(env):
+    """Points within 2^-64 of an integer take the long-division path: r = 2^-53 mod n and
+    D = ceil((n - r) 2^53 / n) give the smallest positive fraction 1/(n 2^53)."""
+    q, torch, dev, _ = env
+    for n in (108863, 1024565021, 2147483647, 2305843009213693951):
+        r = pow(2 ** 53, -1, n)
+        D = -(-((n - r) << 53) // n)
+        assert D < 2 ** 53
+        Dm = np.array([[D]], dtype=np.uint64)
+        rr = q.rule(n, [1], _dev_shifts(torch, Dm, dev))
+        i0 = max(0, r - 1)
+        cnt = min(3, n - i0)
+        out = torch.empty(cnt, dtype=torch.float64, device=dev)
+        q.points(rr, i0, cnt, out)
+        got = out.cpu().numpy()
+        ref = O.points(n, [1], Dm, i0, cnt).reshape(-1)
+        assert np.array_equal(got.view(np.uint64), ref.view(np.uint64))
+        assert got[r - i0] == O.point_py(r, n, D) and 0 < got[r - i0] < 2.0 ** -64
+
+
+def test_points_fig1_lattice(env):
+    q, torch, dev, _ = env
+    D = np.zeros((1, 2), dtype=np.uint64)
+    r = q.rule(55, [1, 34], _dev_shifts(torch, D, dev))
+    out = torch.empty(55 * 2, dtype=torch.float64, device=dev)
+    q.points(r, 0, 55, out)
+    p = out.cpu().numpy().reshape(55, 2)
+    assert all(p[i, 0] == i / 55 and p[i, 1] == (34 * i % 55) / 55 for i in range(55))
+
+
+# ---------------------------------------------------------------------------------------
+GENZ_CASES = [(fam, d, tr) for fam in (1, 2, 3, 4) for d in (2, 6, 10)
+              for tr in (("korobov", 3), ("baker",))] + \
+             [(1, 8, ("korobov", 1)), (4, 8, ("korobov", 2)), (3, 6, ("korobov", 4)),
+              (2, 4, ("none",)), (5, 5, ("korobov", 3)), (6, 4, ("baker",)),
+              (2, 3, ("sidi", 2)), (1, 3, ("sidi", 3)), (4, 5, ("korobov", 2, 5)),
+              (2, 16, ("baker",)), (3, 1, ("korobov", 3))]
+
+
+@pytest.mark.parametrize("fam,d,tr", GENZ_CASES)
+def test_genz_sums_match_oracle(env, fam, d, tr):
+    q, torch, dev, tab = env
+    n = 4691
+    c, w = W.genz_params(fam, d, 17 + d)
+    m = 8
+    D = O.shifts(100 + fam * 7 + d, m, d)
+    z = tab.z_for(n)[:d]
+    res, gre, _, cnt = _gpu_sums(env, q.Integrand.genz(fam, c, w), n, z, D, tr)
+    o = O.shift_sums(O.genz(fam, c, w), tr, n, z, D)
+    Qg, Qo, A = _compare(gre, None, o, n)
+    qbar, sig = O.shift_reduce(Qo)
+    assert abs(res[0] - qbar) <= TOL * A.mean()
+    assert abs(res[1] - sig) <= max(1e-9 * sig, 2e-12 * A.mean())
+    assert cnt[0] == 0
+
+
+def test_config1_product_peak_full_size(env):
+    """d = 4 product peak, c = 5, Korobov-3, n = 108863, m = 16: whole lattice against the
+    oracle and the closed form."""
+    q, torch, dev, tab = env
+    n, d, m = 108863, 4, 16
+    c, w = W.product_peak_params(d, 1)
+    D = O.shifts(2024, m, d)
+    z = tab.z_for(n)[:d]
+    res, gre, _, _ = _gpu_sums(env, q.Integrand.genz(2, c, w), n, z, D, ("korobov", 3))
+    o = O.shift_sums(O.genz(2, c, w), ("korobov", 3), n, z, D)
+    _compare(gre, None, o, n)
+    exact = CF.genz_exact(2, c, w)
+    assert abs(res[0] - exact) <= 5 * res[1]
+
+
+def test_ragged_ranges_and_sharding(env):
+    """Arbitrary i-ranges (partial tiles, ragged tails) match the oracle on the same range,
+    and ranges that split [0, n) add up to the whole."""
+    q, torch, dev, tab = env
+    n, d, m = 108863, 6, 5
+    c, w = W.genz_params(4, d, 3)
+    D = O.shifts(5, m, d)
+    z = tab.z_for(n)[:d]
+    f = q.Integrand.genz(4, c, w)
+    parts = []
+    for a, b in [(0, 1), (0, 37), (12345, 12345 + 4097), (n - 1000, n), (0, 50000), (50000, n)]:
+        _, gre, _, _ = _gpu_sums(env, f, n, z, D, ("korobov", 3), i0=a, i1=b)
+        o = O.shift_sums(O.genz(4, c, w), ("korobov", 3), n, z, D, i0=a, i1=b)
+        A = o["abs"]
+        Sg = gre[:, 0] + gre[:, 1]
+        So = o["re"][:, 0] + o["re"][:, 1]
+        assert np.all(np.abs(Sg - So) <= TOL * A)
+        parts.append(Sg)
+    _, full, _, _ = _gpu_sums(env, f, n, z, D, ("korobov", 3))
+    Sfull = full[:, 0] + full[:, 1]
+    assert np.allclose(parts[-2] + parts[-1], Sfull, rtol=1e-15, atol=0)
+
+
+def test_deterministic(env):
+    q, torch, dev, tab = env
+    n, d, m = 108863, 8, 32
+    c, w = W.genz_params(1, d, 9)
+    D = O.shifts(1, m, d)
+    z = tab.z_for(n)[:d]
+    f = q.Integrand.genz(1, c, w)
+    a = _gpu_sums(env, f, n, z, D, ("baker",))
+    b = _gpu_sums(env, f, n, z, D, ("baker",))
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[0], b[0])
+
+
+@pytest.mark.parametrize("m", [2, 3, 10, 32, 33, 300, 1024])
+def test_shift_counts(env, m):
+    """m from the minimum (2) past one block (256) to the maximum (1024 = 4 launches)."""
+    q, torch, dev, tab = env
+    n, d = 1021, 3
+    c, w = W.genz_params(2, d, m)
+    D = O.shifts(m, m, d)
+    z = tab.z_for(n)[:d]
+    _, gre, _, _ = _gpu_sums(env, q.Integrand.genz(2, c, w), n, z, D, ("korobov", 2))
+    o = O.shift_sums(O.genz(2, c, w), ("korobov", 2), n, z, D)
+    _compare(gre, None, o, n)
+
+
+def test_trig_exactness_on_gpu(env):
+    """Lattice exactness: the GPU rule integrates the trigonometric product (no dual-lattice
+    frequency) to 1 up to rounding, and reproduces the predicted value when h is in the
+    dual lattice."""
+    q, torch, dev, tab = env
+    n = 1021
+    z = [int(v) for v in tab.z_for(n)]
+    amp, h, th = W.trig_product_params(4, 7)
+    D = O.shifts(3, 4, 4)
+    _, gre, _, _ = _gpu_sums(env, q.Integrand.trig(amp, h, th), n, z[:4], D, ("none",))
+    Q = (gre[:, 0] + gre[:, 1]) / n
+    for k in range(4):
+        pred = CF.trig_lattice_exact(amp, h, th, n, z[:4], D[k].astype(float) / 2 ** 53).real
+        assert abs(Q[k] - pred) < 1e-13
+    h2 = np.array([n - z[1], 1])
+    amp2 = np.array([0.6, 0.7])
+    th2 = np.array([0.13, 0.71])
+    D2 = O.shifts(5, 6, 2)
+    _, g2, _, _ = _gpu_sums(env, q.Integrand.trig(amp2, h2, th2), n, z[:2], D2, ("none",))
+    Q2 = (g2[:, 0] + g2[:, 1]) / n
+    for k in range(6):
+        pred = CF.trig_lattice_exact(amp2, h2, th2, n, z[:2], D2[k].astype(float) / 2 ** 53).real
+        assert abs(Q2[k] - pred) < 1e-11
+
+
+def test_minimal_example(env):
+    q, torch, dev, tab = env
+    out = q.integrate(q.Integrand.monomial(3), tab, 8191, 16, ("korobov", 3), seed=1)
+    assert abs(out["value"] - 0.125) <= max(5 * out["err"], 1e-14)
+    assert out["n"] == q.get_next_n(tab, 8191)
+
+
+def test_fit_apply_matches_oracle(env):
+    q, torch, dev, tab = env
+    n, d, m = 4691, 4, 6
+    c, w = W.genz_params(2, d, 2)
+    P = W.fit_params_example(d, 3)
+    D = O.shifts(8, m, d)
+    z = tab.z_for(n)[:d]
+    for tr in (("korobov", 3), ("baker",), ("none",)):
+        _, gre, _, _ = _gpu_sums(env, q.Integrand.genz(2, c, w), n, z, D, tr, fitp=P)
+        o = O.shift_sums(O.genz(2, c, w), tr, n, z, D, fitp=P)
+        _compare(gre, None, o, n)
+
+
+def test_feynman_complex_matches_oracle(env):
+    q, torch, dev, tab = env
+    fl = W.feynman_like(3)
+    n, d, m = 4691, 5, 4
+    D = O.shifts(12, m, d)
+    z = tab.z_for(n)[:d]
+    res, gre, gim, cnt = _gpu_sums(env, q.Integrand.polynomial(fl), n, z, D, ("korobov", 3))
+    o = O.shift_sums(O.feynman_complex(fl), ("korobov", 3), n, z, D)
+    _compare(gre, gim, o, n, is_complex=True, tol=1e-11)
+    assert cnt[1] == o["signfail"]
+
+
+def test_sector_real_matches_oracle(env):
+    q, torch, dev, tab = env
+    fl = W.sector_like(4, 6, 40, 120)
+    n, d, m = 4691, 6, 4
+    D = O.shifts(13, m, d)
+    z = tab.z_for(n)[:d]
+    _, gre, _, _ = _gpu_sums(env, q.Integrand.polynomial(fl), n, z, D, ("korobov", 2))
+    o = O.shift_sums(O.from_feynman(fl), ("korobov", 2), n, z, D)
+    _compare(gre, None, o, n)
+
+
+def test_evaluate_matches_oracle(env):
+    q, torch, dev, tab = env
+    n, d = 4691, 5
+    c, w = W.genz_params(3, d, 1)
+    D1 = O.shifts(4, 1, d)[0]
+    z = tab.z_for(n)[:d]
+    out = torch.empty(1000, dtype=torch.float64, device=dev)
+    f = q.Integrand.genz(3, c, w)
+    q.evaluate(f.device_struct(dev), n, z, torch.from_numpy(D1.astype(np.int64)).to(dev), 100, 1000, out)
+    ref = O.evaluate(O.genz(3, c, w), n, z, D1, 100, 1000)
+    got = out.cpu().numpy()
+    assert np.all(np.abs(got - ref) <= 2e-15 * np.abs(ref))
+
+
+def test_histogram_matches_oracle(env):
+    q, torch, dev, tab = env
+    n, d, bins = 108863, 4, 1000
+    c, w = W.genz_params(2, d, 5)
+    D1 = O.shifts(6, 1, d)[0]
+    z = tab.z_for(n)[:d]
+    f = q.Integrand.genz(2, c, w)
+    hist = torch.empty(d * bins, dtype=torch.float64, device=dev)
+    ws = torch.empty(q.histogram_workspace_bytes(n, d, bins), dtype=torch.uint8, device=dev)
+    q.histogram(f.device_struct(dev), n, z, torch.from_numpy(D1.astype(np.int64)).to(dev), bins, hist, ws)
+    ref = O.histogram(O.genz(2, c, w), n, z, D1, bins)
+    got = hist.cpu().numpy().reshape(d, bins)
+    assert np.all(np.abs(got - ref) <= 1e-13 * np.abs(ref) + 1e-15 * ref.max())
+
+
+def test_integrate_with_fit_reduces_error(env):
+    """Case with the variance-reduction fit: the fitted integrand integrates to the same
+    value (closed form) and the fit runs end to end through qmc_integrate."""
+    q, torch, dev, tab = env
+    c, w = W.genz_params(2, 3, 8)
+    f = q.Integrand.genz(2, c, w)
+    exact = CF.genz_exact(2, c, w)
+    plain = q.integrate(f, tab, 108863, 16, ("korobov", 1), seed=3)
+    fit = q.integrate(f, tab, 108863, 16, ("korobov", 1), fit=q.fit_options(), seed=3)
+    assert abs(plain["value"] - exact) <= 6 * plain["err"]
+    assert abs(fit["value"] - exact) <= 6 * fit["err"] + 1e-12 * abs(exact)
+
+
+def test_adaptive_case1_reaches_goal(env):
+    q, torch, dev, tab = env
+    c, w = W.genz_params(4, 5, 2)
+    f = q.Integrand.genz(4, c, w)
+    exact = CF.genz_exact(4, c, w)
+    out = q.integrate(f, tab, 1021, 16, ("korobov", 3), seed=5,
+                      opts=q.options(epsrel=1e-8, epsabs=0.0, maxeval=10**10))
+    assert out["err"] <= 1e-8 * abs(out["value"])
+    assert out["iterations"] >= 2
+    assert abs(out["value"] - exact) <= 10 * out["err"]
+
+
+def test_adaptive_respects_maxeval(env):
+    q, torch, dev, tab = env
+    c, w = W.genz_params(1, 8, 2)
+    out = q.integrate(q.Integrand.genz(1, c, w), tab, 1021, 8, ("korobov", 1), seed=5,
+                      opts=q.options(epsrel=1e-15, epsabs=0.0, maxeval=2_000_000))
+    assert out["evaluations"] <= 2_000_000 + out["n"] * out["m"]
+
+
+def test_nonfinite_counted(env):
+    """U/F^2.5 with F = x_1 is infinite at the lattice point x = 0 (zero shift): every such
+    sample is counted, once per shift."""
+    q, torch, dev, tab = env
+    n, m = 1021, 4
+    f = q.Integrand("sector", 1, ucoef=np.array([1.0]), uexp=np.zeros((1, 1), np.int32),
+                    fcoef=np.array([1.0]), fexp=np.ones((1, 1), np.int32), pa=1.0, pb=2.5)
+    D = np.zeros((m, 1), dtype=np.uint64)
+    _, _, _, cnt = _gpu_sums(env, f, n, [1], D, ("none",))
+    assert cnt[0] == m
+
+
+@pytest.mark.parametrize("tr", [("korobov", 3), ("baker",)])
+def test_bench_size_sampled_subranges(env, tr):
+    """At the benchmark's size (n = 10560653, m = 32, d = 10), the full-range GPU result is
+    checked on sampled sub-ranges the oracle can afford, and the whole against the closed
+    form."""
+    q, torch, dev, tab = env
+    n, d, m = 10560653, 10, 32
+    fam = 4
+    c, w = W.genz_params(fam, d, 1)
+    D = O.shifts(77, m, d)
+    z = tab.z_for(n)[:d]
+    f = q.Integrand.genz(fam, c, w)
+    res, full, _, _ = _gpu_sums(env, f, n, z, D, tr)
+    exact = CF.genz_exact(fam, c, w)
+    assert abs(res[0] - exact) <= 6 * res[1] + 1e-13 * abs(exact)
+    rng = np.random.default_rng(1)
+    for _ in range(3):
+        a = int(rng.integers(0, n - 3000))
+        b = a + int(rng.integers(1, 3000))
+        _, gre, _, _ = _gpu_sums(env, f, n, z, D, tr, i0=a, i1=b)
+        o = O.shift_sums(O.genz(fam, c, w), tr, n, z, D, i0=a, i1=b)
+        assert np.all(np.abs((gre[:, 0] + gre[:, 1]) - (o["re"][:, 0] + o["re"][:, 1])) <= TOL * o["abs"])

@@ -76,13 +76,29 @@ def fp64_flops_per_eval(family: int, transform, d: int) -> int:
     return tr + fam + 2
 
 
-def workload_items(rank: int = 0):
+def parse_transform(tok: str):
+    if tok == "baker":
+        return ("baker",)
+    if tok.startswith("korobov"):
+        return ("korobov", int(tok[len("korobov"):]))
+    raise ValueError(tok)
+
+
+def workload_items(rank: int = 0, only: str | None = None):
+    """The 45 (family, d, transform) integrals, or the single one named by ``only``
+    ("FAMILY:D:TRANSFORM", e.g. "4:10:korobov3") for profiling a small case."""
     items = []
     for fam in FAMILIES:
         for d in DIMS:
             c, w = W.genz_params(fam, d, 1000 + 17 * rank + d)
             for tr in TRANSFORMS:
                 items.append((fam, d, tr, c, w))
+    if only:
+        f, d, t = only.split(":")
+        key = (int(f), int(d), parse_transform(t))
+        items = [it for it in items if (it[0], it[1], it[2]) == key]
+        if not items:
+            raise ValueError(f"--only {only} names no workload item")
     return items
 
 
@@ -152,9 +168,9 @@ def run_gpu(args, rank: int, world: int):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     table = q.GenvecTable.load()
-    n = N_LATTICE
+    n = args.n
     zfull = table.z_for(n)
-    items = workload_items(rank)
+    items = workload_items(rank, args.only)
     stream = torch.cuda.current_stream(dev)
 
     # resident inputs: coefficients, shifts, workspace, outputs
@@ -231,7 +247,7 @@ def run_gpu(args, rank: int, world: int):
     # e2e through qmc_integrate with host buffers
     e2e_ms = []
     h2d = 0
-    for it in range(args.e2e_steps + 1):
+    for it in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for (fam, d, tr, f, fd, r, Dd, D), (_, _, _, c, w) in zip(prepared, items):
@@ -298,6 +314,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-kernel-events", dest="kernel_events", action="store_false")
+    ap.add_argument("--only", default=None, help="FAMILY:D:TRANSFORM, e.g. 4:10:korobov3")
+    ap.add_argument("--n", type=int, default=N_LATTICE, help="lattice size (a table size)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -305,9 +323,10 @@ def main():
     base = {"metric": "FP64 integrand evals/sec", "unit": "evals/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "genz_osc_corner_gauss_d6_8_10_baker_korobov1-4_n10560653_m32",
-                       "integrals_per_step": len(FAMILIES) * len(DIMS) * len(TRANSFORMS),
-                       "n": N_LATTICE, "m": M_SHIFTS, "l2": "flushed between steps",
+            "config": {"workload": (f"genz_osc_corner_gauss_d6_8_10_baker_korobov1-4_n{args.n}_m32"
+                                    if not args.only else f"genz_{args.only}_n{args.n}_m32"),
+                       "integrals_per_step": len(workload_items(0, args.only)),
+                       "n": args.n, "m": M_SHIFTS, "l2": "flushed between steps",
                        "parallelism": f"replicas x{args.gpus} (independent integrals per rank)"}}
 
     if args.impl == "reference":
@@ -345,7 +364,8 @@ def main():
     r = run_gpu(args, rank, world)
     evals_total = r["evals_per_step"] * args.steps * world
     value = evals_total / (r["total_ms"] / 1e3)
-    e2e_value = r["evals_per_step"] * r["e2e_steps"] * world / (r["e2e_total_ms"] / 1e3)
+    e2e_value = (r["evals_per_step"] * r["e2e_steps"] * world / (r["e2e_total_ms"] / 1e3)
+                 if r["e2e_total_ms"] > 0 else None)
     clk = r["clocks"]
     sm_mhz = clk.get("sm_mhz") or SM_MAX_MHZ
     peak_max = SM_COUNT * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e9   # GFLOP/s
@@ -371,8 +391,8 @@ def main():
                        "reasons": clk.get("reasons")},
             "nonfinite": r["nonfinite"],
         })
-        if world == 1:
-            line["cpu_baseline"] = cpu_baseline(args.cpu_budget, workload_items(0))
+        if world == 1 and args.cpu_budget > 0:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_budget, workload_items(0, args.only))
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -9,10 +9,13 @@
 //   J_kl = dz_k/dx_l = delta_kl - i lam [delta_kl (1 - 2 x_k) dF_k + x_k (1 - x_k) d2F_kl],
 //   f = U(z)^a F(z)^-b det J   (principal branch),
 // the contour deformation used for Feynman-parameter integrals with an F that changes sign
-// (the "F - i delta" prescription realised by the deformation).  J = I - i lam M with M
-// real symmetric, so J has Hermitian part I: Gaussian elimination without pivoting cannot
-// break down and every pivot has positive real part; the determinant uses a symmetric
-// (LDL^T) elimination.
+// (the "F - i delta" prescription realised by the deformation).  J = I - i lam (D H + E)
+// with D = diag(x (1 - x)), E = diag((1 - 2x) dF) and H the (symmetric) Hessian of F.  The
+// diagonal similarity D^(1/2) (.) D^(-1/2) maps J to I - i lam (D^(1/2) H D^(1/2) + E),
+// whose Hermitian part is I; leading principal minors, hence the pivots of Gaussian
+// elimination, are unchanged by the similarity, so elimination on J without pivoting
+// cannot break down (every pivot has real part >= 1 in the symmetrised form) and
+// det J is the product of the pivots.
 #pragma once
 #include <cstdint>
 
@@ -188,13 +191,13 @@ static __device__ __noinline__ void feynman_value(const double *xin, int d, cons
         F.im = fma(ps.fcoef[q], t.im, F.im);
     }
     if (F.im > 0.0) ++signfail;
-    // J = I - i lam M, M_kl = delta_kl (1 - 2 x_k) dF_k + x_k (1 - x_k) d2F_kl; symmetric
-    // elimination on the upper triangle, det = product of pivots.
+    // J_kl = delta_kl - i lam [delta_kl (1 - 2 x_k) dF_k + x_k (1 - x_k) d2F_kl]; Gaussian
+    // elimination without pivoting, det = product of the pivots.
     cplx A[kMaxDim * kMaxDim];
 #pragma unroll 1
     for (int k = 0; k < d; ++k)
 #pragma unroll 1
-        for (int l = k; l < d; ++l) {
+        for (int l = 0; l < d; ++l) {
             double mkl = xo[k] * H[k * d + l];
             if (k == l) mkl = fma(1.0 - 2.0 * x[k], grad[k], mkl);
             A[k * d + l] = {(k == l) ? 1.0 : 0.0, -lam * mkl};
@@ -208,9 +211,9 @@ static __device__ __noinline__ void feynman_value(const double *xin, int d, cons
         cplx inv = crecip(piv);
 #pragma unroll 1
         for (int r = c + 1; r < d; ++r) {
-            cplx l = cmul(A[c * d + r], inv);    // a_rc / a_cc with a_rc = a_cr
+            cplx l = cmul(A[r * d + c], inv);
 #pragma unroll 1
-            for (int q = r; q < d; ++q) {
+            for (int q = c + 1; q < d; ++q) {
                 cplx a = A[c * d + q];
                 cplx &t = A[r * d + q];
                 t.re -= fma(l.re, a.re, -l.im * a.im);

@@ -175,6 +175,7 @@ class Integrand:
         s.ucoef, s.fcoef = _ptr(arrs["ucoef"]), _ptr(arrs["fcoef"])
         s.uexp, s.fexp = _ptr(arrs["uexp"]), _ptr(arrs["fexp"])
         s.pa, s.pb, s.lambda_ = self.pa, self.pb, self.lam
+        s._keep = arrs   # the struct holds raw addresses: keep the arrays alive with it
         return s
 
     def _arrays(self) -> dict:

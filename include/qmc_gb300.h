@@ -38,6 +38,7 @@ extern "C" {
 #define QMC_MAX_DIM 16      /* integration variables per integrand */
 #define QMC_MAX_SHIFTS 1024 /* random shifts m (the paper's maxmperpackage default) */
 #define QMC_MAX_TERMS 512   /* monomials per polynomial (U and F each) */
+#define QMC_NOALLOC_SCRATCH_BYTES (8u << 20) /* fixed device scratch of qmc_sums_noalloc */
 
 /* ---- status codes ------------------------------------------------------------------ */
 enum {
@@ -185,6 +186,25 @@ size_t qmc_sums_workspace_bytes(const qmc_rule *rule, int is_complex, uint64_t i
 int qmc_sums(const qmc_integrand *f, const qmc_rule *rule, uint64_t i_begin, uint64_t i_end,
              void *workspace, size_t workspace_bytes, double *sums,
              unsigned long long *counters, void *stream);
+
+/* qmc_sums without a workspace argument and without any allocation.  The paper has no
+ * counterpart: it is for callers that cannot allocate device memory when they integrate
+ * -- code running under CUDA-graph capture, latency- or signal-critical paths, hosts whose
+ * device memory belongs to another allocator, or deployments that fix all device memory
+ * in advance.  Same inputs, outputs and results as qmc_sums (bit-identical sums); the
+ * per-tile partials live in a fixed device array of QMC_NOALLOC_SCRATCH_BYTES (8 MiB) that
+ * every GPU loading the library holds until the process exits.
+ *   - Problems whose partials need more than that (qmc_sums_workspace_bytes() >
+ *     QMC_NOALLOC_SCRATCH_BYTES, e.g. real m = 32 beyond n ~ 2e9) are rejected with
+ *     QMC_ERR_WORKSPACE before anything is launched.
+ *   - The first call on a device looks up the array's device address (once per device,
+ *     with that device current); make that first call before any stream capture.
+ *   - All calls on a device share the array and it keeps the last call's contents; the
+ *     kernel overwrites every partial it reads, so nothing has to be cleared first.  Calls
+ *     that overlap on the GPU (unordered streams or threads) race on it: order them.
+ *   - It calls no cudaMalloc, cudaFree or allocating library routine. */
+int qmc_sums_noalloc(const qmc_integrand *f, const qmc_rule *rule, uint64_t i_begin,
+                     uint64_t i_end, double *sums, unsigned long long *counters, void *stream);
 
 /* Shift reduction (Eq. (lattice) and Eq. (lattice-error)) from device sums laid out as
  * above over a lattice of size n: result (device) [4] = Qbar_re, sigma_re, Qbar_im,

@@ -23,7 +23,8 @@ from ._capi import (FAMILY, QMC_MAX_DIM, STATUS, TRANSFORM, qmc_fit_opts, qmc_ge
                     qmc_integrand, qmc_options, qmc_result, qmc_rule, qmc_transform)
 
 __all__ = ["QMCError", "lib", "GenvecTable", "Integrand", "make_transform", "get_next_n",
-           "make_shifts", "rule", "points", "sums_workspace_bytes", "sums", "finalize",
+           "make_shifts", "rule", "points", "sums_workspace_bytes", "sums", "sums_noalloc",
+           "finalize",
            "evaluate", "histogram_workspace_bytes", "histogram", "fit_polysingular",
            "integrate", "integrate_device", "DEFAULT_TABLE"]
 
@@ -239,6 +240,17 @@ def sums(f: qmc_integrand, r: qmc_rule, i_begin: int, i_end: int, workspace, out
     nbytes = workspace.numel() * workspace.element_size()
     _check(lib().qmc_sums(C.byref(f), C.byref(r), int(i_begin), int(i_end), _ptr(workspace), nbytes,
                           _ptr(out), _ptr(counters), _stream(stream)), "sums")
+    return out
+
+
+def sums_noalloc(f: qmc_integrand, r: qmc_rule, i_begin: int, i_end: int, out, counters=None,
+                 stream=None):
+    """qmc_sums_noalloc: the per-shift sums with the library's fixed device scratch instead
+    of a caller workspace, for callers that cannot allocate (graph capture, preallocated
+    deployments).  Raises QMCError(QMC_ERR_WORKSPACE) when the problem needs more than
+    QMC_NOALLOC_SCRATCH_BYTES of partials; calls on one device must not overlap."""
+    _check(lib().qmc_sums_noalloc(C.byref(f), C.byref(r), int(i_begin), int(i_end), _ptr(out),
+                                  _ptr(counters), _stream(stream)), "sums_noalloc")
     return out
 
 

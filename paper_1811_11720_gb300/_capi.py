@@ -10,6 +10,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libqmc_gb300.so")
 QMC_MAX_DIM = 16
 QMC_MAX_SHIFTS = 1024
 QMC_MAX_TERMS = 512
+QMC_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 STATUS = {
     0: "QMC_OK", -1: "QMC_ERR_ARG", -2: "QMC_ERR_DIM", -3: "QMC_ERR_N", -4: "QMC_ERR_GENVEC",
@@ -80,6 +81,8 @@ PROTOTYPES = {
     "qmc_sums_workspace_bytes": (C.c_size_t, [_P(qmc_rule), C.c_int, C.c_uint64, C.c_uint64]),
     "qmc_sums": (C.c_int, [_P(qmc_integrand), _P(qmc_rule), C.c_uint64, C.c_uint64, C.c_void_p,
                            C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "qmc_sums_noalloc": (C.c_int, [_P(qmc_integrand), _P(qmc_rule), C.c_uint64, C.c_uint64,
+                                   C.c_void_p, C.c_void_p, C.c_void_p]),
     "qmc_finalize": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int, C.c_void_p,
                                C.c_void_p, C.c_void_p]),
     "qmc_evaluate": (C.c_int, [_P(qmc_integrand), C.c_uint64, C.c_void_p, C.c_int, C.c_void_p,

@@ -28,17 +28,21 @@ __device__ __forceinline__ double twice(double y) {
     return __longlong_as_double((long long)(b ? b + 0x0010000000000000ull : 0ull));
 }
 
-// x^e for a small non-negative integer e (uniform across the warp): binary powering.
+// x^e for a small non-negative integer e (uniform across the warp): left-to-right binary
+// powering, floor(log2 e) squarings plus one multiply per further set bit.
 __device__ __forceinline__ double ipow_u(double x, int e) {
-    double r = 1.0;
-    double b = x;
+    if (e <= 0) return 1.0;
+    const int top = 31 - __clz(e);
+    double r = x;
 #pragma unroll 1
-    while (e) {
-        if (e & 1) r *= b;
-        e >>= 1;
-        if (e) b *= b;
+    for (int b = top - 1; b >= 0; --b) {
+        r *= r;
+        if ((e >> b) & 1) r *= x;
     }
     return r;
 }
+
+// Select between two doubles on the integer pipe.
+__device__ __forceinline__ double sel(bool p, double a, double b) { return p ? a : b; }
 
 }  // namespace qmc

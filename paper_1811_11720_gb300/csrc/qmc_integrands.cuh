@@ -4,18 +4,32 @@
 // trigonometric product used by the lattice-exactness tests, and the polynomial
 // (sector-like) families.  Separable families are evaluated while the coordinates are
 // produced (FamilyAcc::add per dimension), so no coordinate array is kept; the polynomial
-// families store x in registers and evaluate U and F in finish().
+// families store x and evaluate U and F in finish().
+//
+// add() receives the coordinate in reflected form (x = y or x = 1 - y, see
+// qmc_transforms.cuh).  The Genz families fold the reflection into their own fused
+// multiply-add with per-dimension constants staged in shared memory:
+//   c (x - w) = (+-c) y + (-c w  or  c (1 - w)),
+// and for the linear forms sum c_j x_j the constant part, the sum of c_j over reflected
+// dimensions, is read from two 256-entry subset-sum tables (dimensions 0-7 and 8-15)
+// indexed by the reflection bit mask.
 #pragma once
 #include <cstdint>
 
 #include "qmc_fp.cuh"
 #include "qmc_params.cuh"
 #include "qmc_poly.cuh"
+#include "qmc_transforms.cuh"
 
 namespace qmc {
 
 struct FamilyShared {
     double c[kMaxDim], w[kMaxDim], aux[kMaxDim];
+    double mcw[kMaxDim];    // -c w
+    double c1w[kMaxDim];    // c (1 - w)
+    double w1[kMaxDim];     // 1 - w
+    double sub_lo[256];     // sum of c_j over the set bits j of the index, j < 8
+    double sub_hi[256];     // the same for j = 8 + bit
     double s0;
     int64_t h[kMaxDim];
     PolyShared poly;
@@ -32,26 +46,54 @@ __device__ __forceinline__ void stage_family(const SumsParams &p, FamilyShared &
             double w = p.w ? p.w[tid] : 0.0;
             fs.c[tid] = c;
             fs.w[tid] = w;
+            fs.mcw[tid] = -(c * w);
+            fs.c1w[tid] = c * (1.0 - w);
+            fs.w1[tid] = 1.0 - w;
             if constexpr (FAM == QMC_GENZ_PRODUCT_PEAK) fs.aux[tid] = 1.0 / (c * c);
             fs.h[tid] = p.h ? p.h[tid] : 0;
         }
         if (tid == 0) fs.s0 = (FAM == QMC_GENZ_OSCILLATORY && p.w) ? 6.283185307179586476925 * p.w[0] : 0.0;
+        if constexpr (FAM == QMC_GENZ_OSCILLATORY || FAM == QMC_GENZ_CORNER_PEAK ||
+                      FAM == QMC_GENZ_DISCONTINUOUS) {
+            for (int b = tid; b < 256; b += blockDim.x) {
+                double lo = 0.0, hi = 0.0;
+                for (int j = 0; j < 8; ++j) {
+                    if ((b >> j) & 1) {
+                        if (j < p.d) lo += p.c[j];
+                        if (j + 8 < p.d) hi += p.c[j + 8];
+                    }
+                }
+                fs.sub_lo[b] = lo;
+                fs.sub_hi[b] = hi;
+            }
+        }
     }
 }
 
 template <int FAM>
 struct FamilyAcc;
 
+// sum of c_j over reflected dimensions
+__device__ __forceinline__ double reflected_c_sum(uint32_t mask, int d, const FamilyShared &fs) {
+    double r = fs.sub_lo[mask & 255u];
+    if (d > 8) r += fs.sub_hi[(mask >> 8) & 255u];
+    return r;
+}
+
 // 1: cos(2 pi w_1 + sum c_i x_i)
 template <>
 struct FamilyAcc<QMC_GENZ_OSCILLATORY> {
     static constexpr bool kComplex = false;
     double s;
-    __device__ __forceinline__ void init(const FamilyShared &fs) { s = fs.s0; }
-    __device__ __forceinline__ void add(int j, double x, const FamilyShared &fs) { s = fma(fs.c[j], x, s); }
-    __device__ __forceinline__ void finish(int, const FamilyShared &, double &re, double &im,
+    uint32_t mask;
+    __device__ __forceinline__ void init(const FamilyShared &fs) { s = fs.s0; mask = 0; }
+    __device__ __forceinline__ void add(int j, const Mapped &m, const FamilyShared &fs) {
+        s = fma(m.refl ? -fs.c[j] : fs.c[j], m.y, s);
+        mask |= (uint32_t)m.refl << j;
+    }
+    __device__ __forceinline__ void finish(int d, const FamilyShared &fs, double &re, double &im,
                                            unsigned long long &) {
-        re = cos(s);
+        re = cos(mask ? s + reflected_c_sum(mask, d, fs) : s);
         im = 0.0;
     }
 };
@@ -62,8 +104,9 @@ struct FamilyAcc<QMC_GENZ_PRODUCT_PEAK> {
     static constexpr bool kComplex = false;
     double prod;
     __device__ __forceinline__ void init(const FamilyShared &) { prod = 1.0; }
-    __device__ __forceinline__ void add(int j, double x, const FamilyShared &fs) {
-        double t = x - fs.w[j];
+    __device__ __forceinline__ void add(int j, const Mapped &m, const FamilyShared &fs) {
+        // x - w = y - w, or (1 - w) - y when reflected
+        double t = m.refl ? fs.w1[j] - m.y : m.y - fs.w[j];
         prod *= fma(t, t, fs.aux[j]);
     }
     __device__ __forceinline__ void finish(int, const FamilyShared &, double &re, double &im,
@@ -78,11 +121,16 @@ template <>
 struct FamilyAcc<QMC_GENZ_CORNER_PEAK> {
     static constexpr bool kComplex = false;
     double s;
-    __device__ __forceinline__ void init(const FamilyShared &) { s = 1.0; }
-    __device__ __forceinline__ void add(int j, double x, const FamilyShared &fs) { s = fma(fs.c[j], x, s); }
-    __device__ __forceinline__ void finish(int d, const FamilyShared &, double &re, double &im,
+    uint32_t mask;
+    __device__ __forceinline__ void init(const FamilyShared &) { s = 1.0; mask = 0; }
+    __device__ __forceinline__ void add(int j, const Mapped &m, const FamilyShared &fs) {
+        s = fma(m.refl ? -fs.c[j] : fs.c[j], m.y, s);
+        mask |= (uint32_t)m.refl << j;
+    }
+    __device__ __forceinline__ void finish(int d, const FamilyShared &fs, double &re, double &im,
                                            unsigned long long &) {
-        re = 1.0 / ipow_u(s, d + 1);
+        const double t = mask ? s + reflected_c_sum(mask, d, fs) : s;
+        re = 1.0 / ipow_u(t, d + 1);
         im = 0.0;
     }
 };
@@ -93,8 +141,9 @@ struct FamilyAcc<QMC_GENZ_GAUSSIAN> {
     static constexpr bool kComplex = false;
     double s;
     __device__ __forceinline__ void init(const FamilyShared &) { s = 0.0; }
-    __device__ __forceinline__ void add(int j, double x, const FamilyShared &fs) {
-        double q = fs.c[j] * (x - fs.w[j]);
+    __device__ __forceinline__ void add(int j, const Mapped &m, const FamilyShared &fs) {
+        // c (x - w) = c y - c w, or -c y + c (1 - w) when reflected: one fused multiply-add
+        const double q = fma(m.refl ? -fs.c[j] : fs.c[j], m.y, m.refl ? fs.c1w[j] : fs.mcw[j]);
         s = fma(q, q, s);
     }
     __device__ __forceinline__ void finish(int, const FamilyShared &, double &re, double &im,
@@ -110,8 +159,9 @@ struct FamilyAcc<QMC_GENZ_C0> {
     static constexpr bool kComplex = false;
     double s;
     __device__ __forceinline__ void init(const FamilyShared &) { s = 0.0; }
-    __device__ __forceinline__ void add(int j, double x, const FamilyShared &fs) {
-        s = fma(fs.c[j], fabs(x - fs.w[j]), s);
+    __device__ __forceinline__ void add(int j, const Mapped &m, const FamilyShared &fs) {
+        double t = m.refl ? fs.w1[j] - m.y : m.y - fs.w[j];
+        s = fma(fs.c[j], fabs(t), s);
     }
     __device__ __forceinline__ void finish(int, const FamilyShared &, double &re, double &im,
                                            unsigned long long &) {
@@ -125,15 +175,18 @@ template <>
 struct FamilyAcc<QMC_GENZ_DISCONTINUOUS> {
     static constexpr bool kComplex = false;
     double s;
+    uint32_t mask;
     bool zero;
-    __device__ __forceinline__ void init(const FamilyShared &) { s = 0.0; zero = false; }
-    __device__ __forceinline__ void add(int j, double x, const FamilyShared &fs) {
-        if (j < 2) zero |= gt_nonneg(x, fs.w[j]);
-        s = fma(fs.c[j], x, s);
+    __device__ __forceinline__ void init(const FamilyShared &) { s = 0.0; mask = 0; zero = false; }
+    __device__ __forceinline__ void add(int j, const Mapped &m, const FamilyShared &fs) {
+        // x > w is y > w, or (1 - y > w, i.e. y < 1 - w) when reflected
+        if (j < 2) zero |= m.refl ? gt_nonneg(fs.w1[j], m.y) : gt_nonneg(m.y, fs.w[j]);
+        s = fma(m.refl ? -fs.c[j] : fs.c[j], m.y, s);
+        mask |= (uint32_t)m.refl << j;
     }
-    __device__ __forceinline__ void finish(int, const FamilyShared &, double &re, double &im,
+    __device__ __forceinline__ void finish(int d, const FamilyShared &fs, double &re, double &im,
                                            unsigned long long &) {
-        re = zero ? 0.0 : exp(s);
+        re = zero ? 0.0 : exp(mask ? s + reflected_c_sum(mask, d, fs) : s);
         im = 0.0;
     }
 };
@@ -144,7 +197,7 @@ struct FamilyAcc<QMC_MONOMIAL> {
     static constexpr bool kComplex = false;
     double prod;
     __device__ __forceinline__ void init(const FamilyShared &) { prod = 1.0; }
-    __device__ __forceinline__ void add(int, double x, const FamilyShared &) { prod *= x; }
+    __device__ __forceinline__ void add(int, const Mapped &m, const FamilyShared &) { prod *= reflected(m); }
     __device__ __forceinline__ void finish(int, const FamilyShared &, double &re, double &im,
                                            unsigned long long &) {
         re = prod;
@@ -158,8 +211,8 @@ struct FamilyAcc<QMC_TRIG> {
     static constexpr bool kComplex = false;
     double prod;
     __device__ __forceinline__ void init(const FamilyShared &) { prod = 1.0; }
-    __device__ __forceinline__ void add(int j, double x, const FamilyShared &fs) {
-        double a = fma((double)fs.h[j], x, fs.w[j]);
+    __device__ __forceinline__ void add(int j, const Mapped &m, const FamilyShared &fs) {
+        double a = fma((double)fs.h[j], reflected(m), fs.w[j]);
         prod *= fma(fs.c[j], cospi(2.0 * a), 1.0);
     }
     __device__ __forceinline__ void finish(int, const FamilyShared &, double &re, double &im,
@@ -175,7 +228,7 @@ struct FamilyAcc<QMC_SECTOR> {
     static constexpr bool kComplex = false;
     double x[kMaxDim];
     __device__ __forceinline__ void init(const FamilyShared &) {}
-    __device__ __forceinline__ void add(int j, double xv, const FamilyShared &) { x[j] = xv; }
+    __device__ __forceinline__ void add(int j, const Mapped &m, const FamilyShared &) { x[j] = reflected(m); }
     __device__ __forceinline__ void finish(int d, const FamilyShared &fs, double &re, double &im,
                                            unsigned long long &) {
         re = sector_value(x, d, fs.poly);
@@ -189,7 +242,7 @@ struct FamilyAcc<QMC_FEYNMAN> {
     static constexpr bool kComplex = true;
     double x[kMaxDim];
     __device__ __forceinline__ void init(const FamilyShared &) {}
-    __device__ __forceinline__ void add(int j, double xv, const FamilyShared &) { x[j] = xv; }
+    __device__ __forceinline__ void add(int j, const Mapped &m, const FamilyShared &) { x[j] = reflected(m); }
     __device__ __forceinline__ void finish(int d, const FamilyShared &fs, double &re, double &im,
                                            unsigned long long &signfail) {
         feynman_value(x, d, fs.poly, re, im, signfail);

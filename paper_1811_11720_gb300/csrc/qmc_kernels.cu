@@ -146,7 +146,7 @@ __device__ __forceinline__ void eval_point(const FamilyShared &fsh, const double
     fa.init(fsh);
 #pragma unroll
     for (int j = 0; j < kMaxDim; ++j)
-        if (j < d) fa.add(j, x[j], fsh);
+        if (j < d) fa.add(j, Mapped{x[j], false}, fsh);
     fa.finish(d, fsh, re, im, sf);
 }
 

@@ -93,9 +93,9 @@ __global__ void __launch_bounds__(kSumsThreads) sums_kernel(const __grid_constan
 #pragma unroll 1
                 for (int j = 0; j < d; ++j) {
                     double u = fixed_to_double(fhi[j] + dsh[j], flo[j], rem[j], n);
-                    double x = apply_transform<TK>(u, p.t, W);
-                    if (use_fit) x = apply_fit(x, s_fit + kFitStride * j, W.w);
-                    fa.add(j, x, fsh);
+                    Mapped mx = apply_transform<TK>(u, p.t, W);
+                    if (use_fit) mx = Mapped{apply_fit(reflected(mx), s_fit + kFitStride * j, W.w), false};
+                    fa.add(j, mx, fsh);
                     lattice_step(p.dc[j], n, fhi[j], flo[j], rem[j]);
                 }
                 double wt = weight_finish<TK>(W, p.t, cd);

@@ -5,6 +5,12 @@
 // done on the integer pipe: comparisons of non-negative doubles are integer comparisons
 // of their bit patterns, 1 - u for u >= 1/2 (exact by Sterbenz' lemma) and multiplication
 // by 2 are bit manipulations.
+//
+// A transform returns the mapped coordinate in reflected form: x = y (refl == false) or
+// x = 1 - y (refl == true), with y <= 1/2 for the symmetric maps.  Evaluating the Korobov
+// polynomial on v = min(u, 1 - u) keeps relative accuracy at both ends of [0, 1], and the
+// integrands fold the reflection into their own per-dimension fused multiply-add instead
+// of spending an FP64 subtraction on 1 - y.
 #pragma once
 #include <cstdint>
 
@@ -13,33 +19,46 @@
 
 namespace qmc {
 
-// Per-evaluation weight accumulator.  For Korobov the weight prod_j C u_j^r0 (1-u_j)^r1
-// is kept as two running products, prod u_j and prod (1-u_j), raised to r0 and r1 once
-// per evaluation (C^d is folded into the final factor).
+// Per-evaluation weight accumulator.
+//  * Korobov<r,r>: w = C^d prod_j (v_j (1 - v_j))^r, kept as prod_j t_j with
+//    t_j = v_j (1 - v_j) (one fused multiply-add) and raised to r once per evaluation.
+//  * Korobov<r0,r1>: prod u_j and prod (1 - u_j), raised to r0 and r1 once.
+//  * w: other factors (fit Jacobian, Sidi weights).
 struct Weight {
-    double wu, w1, w;   // prod u, prod (1-u), other factors (fit Jacobian, Sidi)
+    double wu, w1, w;
 };
 
+struct Mapped {
+    double y;
+    bool refl;
+};
+
+__device__ __forceinline__ double reflected(const Mapped &m) { return m.refl ? 1.0 - m.y : m.y; }
+
 template <int TK>
-__device__ __forceinline__ double apply_transform(double u, const TransformParams &t, Weight &W) {
+__device__ __forceinline__ Mapped apply_transform(double u, const TransformParams &t, Weight &W) {
     if constexpr (TK == QMC_T_NONE) {
-        return u;
+        return {u, false};
     } else if constexpr (TK == QMC_T_BAKER) {
         // phi(u) = 2u for u <= 1/2, 2 - 2u = 2 (1 - u) otherwise (Eq. (baker)); weight 1.
-        return twice(le_half(u) ? u : one_minus_upper(u));
+        return {twice(le_half(u) ? u : one_minus_upper(u)), false};
     } else if constexpr (TK == QMC_T_KOROBOV) {
+        // phi(u) = v^(e) P(v) with v = u (u <= 1/2, e = r0+1, P = A) or v = 1 - u (reflected,
+        // e = r1+1, P = B); Eq. (korobov) integrated term by term (coefficients on the host).
         const bool lo = le_half(u);
-        const double w1 = 1.0 - u;           // exact for u >= 1/2
-        const double v = lo ? u : w1;
-        const int e = lo ? t.r0 + 1 : t.r1 + 1;
-        double pw = ipow_u(v, e);
+        const double v = lo ? u : one_minus_upper(u);
         double P = lo ? t.A[t.deg] : t.B[t.deg];
 #pragma unroll 1
         for (int q = t.deg - 1; q >= 0; --q) P = fma(P, v, lo ? t.A[q] : t.B[q]);
-        const double ph = pw * P;
-        W.wu *= u;
-        W.w1 *= w1;
-        return lo ? ph : 1.0 - ph;
+        const double y = ipow_u(v, lo ? t.r0 + 1 : t.r1 + 1) * P;
+        if (t.r0 == t.r1) {
+            W.wu *= fma(-v, v, v);            // v (1 - v) = u (1 - u)
+        } else {
+            const double w1v = 1.0 - v;       // rounded for v < 1/2
+            W.wu *= lo ? v : w1v;             // u
+            W.w1 *= lo ? w1v : v;             // 1 - u
+        }
+        return {y, !lo};
     } else {  // QMC_T_SIDI
         // phi = cr I_r(u), I_r = base I_(r mod 2) - (cos(pi u)/pi) sum_q a_q sin^(r-1-2q)
         double s, c;
@@ -58,14 +77,16 @@ __device__ __forceinline__ double apply_transform(double u, const TransformParam
         double I = t.sidi_c[kMaxSidi] * base - c * 0.31830988618379067154 * poly;
         double sr = ipow_u(s, r);
         W.w *= t.C * sr;
-        return t.C * I;
+        return {t.C * I, false};
     }
 }
 
+// cd = C^d for Korobov (folded once per launch).
 template <int TK>
 __device__ __forceinline__ double weight_finish(const Weight &W, const TransformParams &t,
                                                 double cd) {
     if constexpr (TK == QMC_T_KOROBOV) {
+        if (t.r0 == t.r1) return cd * ipow_u(W.wu, t.r0) * W.w;
         return cd * ipow_u(W.wu, t.r0) * ipow_u(W.w1, t.r1) * W.w;
     } else {
         return W.w;

@@ -275,6 +275,111 @@ def run_gpu(args, rank: int, world: int):
     return out
 
 
+def run_batch_workload(args):
+    """Batching (many sector integrals in one launch) against one launch per integral.
+
+    Config-4 shape: `--batch-count` sector integrands U/F^2.5 with positive coefficients,
+    d ~ U{3..8}, U and F of 10..400 monomials each, m = 32, Korobov-3, the
+    variance-reduction fit (histogram + Levenberg-Marquardt) on every second integral, and
+    n log-uniform in [1e4, --batch-nmax] snapped to the table.  Every integral is
+    evaluated twice per step-pair: once inside one batched launch (autotuned shape, replayed
+    from a CUDA graph) and once as separate qmc_sums + qmc_finalize launches (also replayed
+    from a CUDA graph); both reach the same error (same lattices and shifts)."""
+    import torch
+
+    import paper_1811_11720_gb300 as q
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    table = q.GenvecTable.load()
+    rng = np.random.default_rng(args.seed)
+    count = args.batch_count
+    m = M_SHIFTS
+    entries, keep = [], []
+    fit_s = 0.0
+    n_fit = q.get_next_n(table, 100000)
+    z_fit = table.z_for(n_fit)
+    evals = 0
+    for i in range(count):
+        d = int(rng.integers(3, 9))
+        fl = W.sector_like(args.seed + i, d, int(rng.integers(10, 401)), int(rng.integers(10, 401)))
+        f = q.Integrand.polynomial(fl)
+        fs = f.device_struct(dev)
+        n = q.get_next_n(table, int(np.exp(rng.uniform(np.log(1e4), np.log(args.batch_nmax)))))
+        D = q.make_shifts(args.seed + 31 * i, m, d)
+        Dd = torch.from_numpy(D.astype(np.int64)).to(dev)
+        fitd = None
+        if i % 2 == 1:
+            t0 = time.perf_counter()
+            sh = torch.from_numpy(q.make_shifts(args.seed + 31 * i + 1, 1, d)[0].astype(np.int64)).to(dev)
+            hist = torch.empty(d * 1000, dtype=torch.float64, device=dev)
+            hws = torch.empty(q.histogram_workspace_bytes(n_fit, d, 1000), dtype=torch.uint8, device=dev)
+            q.histogram(fs, n_fit, z_fit[:d], sh, 1000, hist, hws)
+            params = q.fit_polysingular(hist.cpu().numpy().reshape(d, 1000))
+            fitd = torch.from_numpy(params).to(dev)
+            fit_s += time.perf_counter() - t0
+        r = q.rule(n, table.z_for(n)[:d], Dd, ("korobov", 3), fitd)
+        entries.append((fs, r, 0, n))
+        keep.append((f, Dd, fitd))
+        evals += n * m
+    b = q.Batch(entries)
+    sums = torch.zeros(count, 4 * m, dtype=torch.float64, device=dev)
+    res = torch.zeros(count, 4, dtype=torch.float64, device=dev)
+    ws0 = torch.empty(b.workspace_bytes(), dtype=torch.uint8, device=dev)
+    cfg = b.autotune(ws0, sums)
+    ws = torch.empty(b.workspace_bytes(cfg), dtype=torch.uint8, device=dev)
+    s = torch.cuda.Stream()
+    plan = b.plan(ws, cfg, stream=s)
+    # single-integral path: one workspace per integral, captured in one graph
+    singles = []
+    for (fs, r, a, bnd) in entries:
+        wsi = torch.empty(max(8, q.sums_workspace_bytes(r, False, a, bnd)), dtype=torch.uint8, device=dev)
+        singles.append((fs, r, a, bnd, wsi))
+    sums1 = torch.zeros(count, 4 * m, dtype=torch.float64, device=dev)
+    res1 = torch.zeros(count, 4, dtype=torch.float64, device=dev)
+
+    def single_pass(stream):
+        for i, (fs, r, a, bnd, wsi) in enumerate(singles):
+            q.sums(fs, r, a, bnd, wsi, sums1[i], None, stream)
+            q.finalize(sums1[i], m, int(r.n), False, res1[i], None, stream)
+
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            plan.run(sums, res, stream=s)
+            single_pass(s)
+    torch.cuda.synchronize()
+    g_b, g_s = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_b, stream=s):
+        plan.run(sums, res, stream=s)
+    with torch.cuda.graph(g_s, stream=s):
+        single_pass(s)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    tb, ts = [], []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        ev[0].record(s); g_b.replay(); ev[1].record(s)
+        ev[2].record(s); g_s.replay(); ev[3].record(s)
+        torch.cuda.synchronize()
+        tb.append(ev[0].elapsed_time(ev[1]))
+        ts.append(ev[2].elapsed_time(ev[3]))
+    same = bool(torch.allclose(res[:, 0], res1[:, 0], rtol=1e-12, atol=0))
+    err_rel = (res[:, 1].abs() / res[:, 0].abs()).median().item()
+    line = {"metric": "batched integrals/s", "unit": "integrals/s",
+            "value": count / (float(np.median(tb)) / 1e3), "higher_is_better": True,
+            "n_gpus": 1, "steps": args.steps, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"sector_batch_{count}_d3-8_terms10-400_n1e4-{args.batch_nmax:.0e}_m32_korobov3_fit_half",
+                       "evaluations": evals, "launch_shape": {"streams_per_block": cfg.streams_per_block,
+                                                              "points_per_stream": cfg.points_per_stream}},
+            "batched_ms": float(np.median(tb)), "per_integral_ms": float(np.median(ts)),
+            "per_integral_integrals_per_s": count / (float(np.median(ts)) / 1e3),
+            "speedup": float(np.median(ts) / np.median(tb)),
+            "evals_per_s_batched": evals / (float(np.median(tb)) / 1e3),
+            "same_results": same, "median_rel_error": err_rel, "fit_setup_s": fit_s,
+            "gpu_launches_batched": 3, "gpu_launches_per_integral": 3 * count}
+    plan.close()
+    print(json.dumps(line))
+
+
 def cpu_baseline(budget_s: float, items, nthreads: int | None = None):
     """The oracle as it stands on the host cores: per-shift sums over a bounded prefix of
     the same lattices, scaled to evaluations per second."""
@@ -316,7 +421,13 @@ def main():
     ap.add_argument("--no-kernel-events", dest="kernel_events", action="store_false")
     ap.add_argument("--only", default=None, help="FAMILY:D:TRANSFORM, e.g. 4:10:korobov3")
     ap.add_argument("--n", type=int, default=N_LATTICE, help="lattice size (a table size)")
+    ap.add_argument("--workload", default="genz", choices=["genz", "batch"])
+    ap.add_argument("--batch-count", type=int, default=2000)
+    ap.add_argument("--batch-nmax", type=float, default=1e5)
     args = ap.parse_args()
+    if args.workload == "batch":
+        run_batch_workload(args)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

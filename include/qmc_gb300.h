@@ -230,6 +230,67 @@ int qmc_histogram(const qmc_integrand *f, uint64_t n, const uint64_t *z, int dim
                   const uint64_t *shift, int bins, double *hist, void *workspace,
                   size_t workspace_bytes, void *stream);
 
+/* ---- batches: many integrals in one launch -------------------------------------------- */
+
+/* One integral of a batch: integrand and rule with device arrays (as for qmc_sums) and
+ * its i-range.  All items of one batch share the integrand family and m (1 <= m <= 256);
+ * dimension, n, z, shifts, transform, fit and coefficients may differ per item.  Families:
+ * Genz 1-4, QMC_SECTOR, QMC_FEYNMAN. */
+typedef struct {
+    qmc_integrand f;
+    qmc_rule rule;
+    uint64_t i_begin, i_end;
+} qmc_batch_item;
+
+/* Launch shape: streams_per_block (block = streams_per_block * m threads, <= 256) and
+ * points_per_stream (points per thread and tile).  0 selects the defaults of qmc_sums
+ * (256/m streams, range-dependent tile length), with which every item's sums are
+ * bit-identical to a qmc_sums call on that item. */
+typedef struct {
+    int streams_per_block;
+    uint32_t points_per_stream;
+} qmc_batch_config;
+
+/* Device workspace for qmc_batch_sums (item descriptors, tile offsets, tile partials);
+ * 0 when the batch is invalid. */
+size_t qmc_batch_workspace_bytes(const qmc_batch_item *items, int count,
+                                 const qmc_batch_config *cfg);
+
+/* Per-shift sums of every item in one kernel launch, then one reduction launch and
+ * (results != NULL) one finalize launch (Eq. (lattice), Eq. (lattice-error)).
+ *   items: host array of count items.  sums (device) [count][4m]: item q's double-double
+ *   sums at q*4m in the qmc_sums layout.  results (device, may be NULL) [count][4]:
+ *   Qbar_re, sigma_re, Qbar_im, sigma_im (needs m >= 2).  counters (device, may be NULL)
+ *   [count][2]: NaN/Inf samples and complex sign-check failures per item, added to.
+ * Errors: argument codes of qmc_sums per item, QMC_ERR_ARG for mixed families or m,
+ * QMC_ERR_WORKSPACE, QMC_ERR_CUDA. */
+int qmc_batch_sums(const qmc_batch_item *items, int count, const qmc_batch_config *cfg,
+                   void *workspace, size_t workspace_bytes, double *sums, double *results,
+                   unsigned long long *counters, void *stream);
+
+/* The same in two steps, for replaying a batch (e.g. from a captured CUDA graph):
+ * qmc_batch_plan_create validates the items, uploads their descriptors into `workspace`
+ * (stream-ordered, then synchronises `stream`) and returns a host handle; the items' device
+ * arrays and the workspace must outlive the plan.  qmc_batch_plan_run enqueues only kernel
+ * launches (batch kernel, reduction, optional finalize), so it can be captured.
+ * qmc_batch_plan_destroy frees the handle (host memory). */
+typedef struct qmc_batch_plan qmc_batch_plan;
+int qmc_batch_plan_create(const qmc_batch_item *items, int count, const qmc_batch_config *cfg,
+                          void *workspace, size_t workspace_bytes, void *stream,
+                          qmc_batch_plan **out);
+int qmc_batch_plan_run(const qmc_batch_plan *plan, double *sums, double *results,
+                       unsigned long long *counters, void *stream);
+void qmc_batch_plan_destroy(qmc_batch_plan *plan);
+
+/* Chooses the launch shape for a batch by timing candidate configurations
+ * (streams_per_block in {256/m, 128/m, 64/m} x points_per_stream in {16..512}) on a sample
+ * of at most 256 items (CUDA events on `stream`).  workspace and sums as for
+ * qmc_batch_sums of the same items (the sample needs no more).  best receives the fastest
+ * configuration.  Overwrites sums. */
+int qmc_batch_autotune(const qmc_batch_item *items, int count, void *workspace,
+                       size_t workspace_bytes, double *sums, void *stream,
+                       qmc_batch_config *best);
+
 /* ---- host entry points -------------------------------------------------------------- */
 
 /* Fit the PolySingular map (Eq. (ISfit), |a2|, |a3| form of App. A.5) per dimension to

@@ -19,14 +19,15 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import _capi
-from ._capi import (FAMILY, QMC_MAX_DIM, STATUS, TRANSFORM, qmc_fit_opts, qmc_genvec_table,
-                    qmc_integrand, qmc_options, qmc_result, qmc_rule, qmc_transform)
+from ._capi import (FAMILY, QMC_MAX_DIM, STATUS, TRANSFORM, qmc_batch_config, qmc_batch_item,
+                    qmc_fit_opts, qmc_genvec_table, qmc_integrand, qmc_options, qmc_result,
+                    qmc_rule, qmc_transform)
 
 __all__ = ["QMCError", "lib", "GenvecTable", "Integrand", "make_transform", "get_next_n",
            "make_shifts", "rule", "points", "sums_workspace_bytes", "sums", "sums_noalloc",
            "finalize",
            "evaluate", "histogram_workspace_bytes", "histogram", "fit_polysingular",
-           "integrate", "integrate_device", "DEFAULT_TABLE"]
+           "integrate", "integrate_device", "Batch", "DEFAULT_TABLE"]
 
 DEFAULT_TABLE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                              "tables", "cbc_korobov_a2_s10.txt")
@@ -338,3 +339,72 @@ def integrate_device(f: Integrand, n: int, z, shifts_dev, transform, fit_dev=Non
     sums(fd, r, i_begin, i_end, workspace, out, cnt, stream)
     finalize(out, m, n, f.is_complex, res, None, stream)
     return res, out, cnt
+
+
+# ----------------------------------------------------------------------------------------
+class Batch:
+    """Many integrals of one family and one m in a single launch (qmc_batch_sums).
+
+    ``entries``: list of (qmc_integrand with device arrays, qmc_rule, i_begin, i_end).
+    The structs (and the tensors they point to) are kept alive by this object."""
+
+    def __init__(self, entries):
+        self.count = len(entries)
+        self.arr = (qmc_batch_item * self.count)()
+        for i, (fs, r, a, b) in enumerate(entries):
+            self.arr[i].f = fs
+            self.arr[i].rule = r
+            self.arr[i].i_begin = int(a)
+            self.arr[i].i_end = int(b)
+        self._keep = entries
+        self.m = int(entries[0][1].m)
+
+    def workspace_bytes(self, cfg: qmc_batch_config | None = None) -> int:
+        return int(lib().qmc_batch_workspace_bytes(self.arr, self.count,
+                                                   None if cfg is None else C.byref(cfg)))
+
+    def sums(self, workspace, sums, results=None, counters=None, cfg=None, stream=None):
+        nbytes = workspace.numel() * workspace.element_size()
+        _check(lib().qmc_batch_sums(self.arr, self.count, None if cfg is None else C.byref(cfg),
+                                    _ptr(workspace), nbytes, _ptr(sums), _ptr(results),
+                                    _ptr(counters), _stream(stream)), "batch_sums")
+        return sums
+
+    def autotune(self, workspace, sums, stream=None) -> qmc_batch_config:
+        best = qmc_batch_config()
+        nbytes = workspace.numel() * workspace.element_size()
+        _check(lib().qmc_batch_autotune(self.arr, self.count, _ptr(workspace), nbytes, _ptr(sums),
+                                        _stream(stream), C.byref(best)), "batch_autotune")
+        return best
+
+    def plan(self, workspace, cfg=None, stream=None) -> "BatchPlan":
+        h = C.c_void_p()
+        nbytes = workspace.numel() * workspace.element_size()
+        _check(lib().qmc_batch_plan_create(self.arr, self.count, None if cfg is None else C.byref(cfg),
+                                           _ptr(workspace), nbytes, _stream(stream), C.byref(h)),
+               "batch_plan_create")
+        return BatchPlan(h, self, workspace)
+
+
+class BatchPlan:
+    """Uploaded batch descriptors; run() enqueues kernels only (graph-capturable)."""
+
+    def __init__(self, handle, batch, workspace):
+        self.handle = handle
+        self._keep = (batch, workspace)
+
+    def run(self, sums, results=None, counters=None, stream=None):
+        _check(lib().qmc_batch_plan_run(self.handle, _ptr(sums), _ptr(results), _ptr(counters),
+                                        _stream(stream)), "batch_plan_run")
+        return sums
+
+    def close(self):
+        if self.handle:
+            lib().qmc_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -59,6 +59,15 @@ class qmc_rule(C.Structure):
                 ("fit", C.c_void_p)]
 
 
+class qmc_batch_item(C.Structure):
+    _fields_ = [("f", qmc_integrand), ("rule", qmc_rule), ("i_begin", C.c_uint64),
+                ("i_end", C.c_uint64)]
+
+
+class qmc_batch_config(C.Structure):
+    _fields_ = [("streams_per_block", C.c_int), ("points_per_stream", C.c_uint32)]
+
+
 class qmc_fit_opts(C.Structure):
     _fields_ = [("enabled", C.c_int), ("evaluateminn", C.c_uint64), ("bins", C.c_int),
                 ("maxiter", C.c_int), ("xtol", C.c_double), ("gtol", C.c_double),
@@ -91,6 +100,15 @@ PROTOTYPES = {
     "qmc_histogram": (C.c_int, [_P(qmc_integrand), C.c_uint64, C.c_void_p, C.c_int, C.c_void_p,
                                 C.c_int, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "qmc_fit_polysingular": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _P(qmc_fit_opts), C.c_void_p]),
+    "qmc_batch_workspace_bytes": (C.c_size_t, [_P(qmc_batch_item), C.c_int, _P(qmc_batch_config)]),
+    "qmc_batch_sums": (C.c_int, [_P(qmc_batch_item), C.c_int, _P(qmc_batch_config), C.c_void_p,
+                                 C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "qmc_batch_autotune": (C.c_int, [_P(qmc_batch_item), C.c_int, C.c_void_p, C.c_size_t,
+                                     C.c_void_p, C.c_void_p, _P(qmc_batch_config)]),
+    "qmc_batch_plan_create": (C.c_int, [_P(qmc_batch_item), C.c_int, _P(qmc_batch_config),
+                                        C.c_void_p, C.c_size_t, C.c_void_p, _P(C.c_void_p)]),
+    "qmc_batch_plan_run": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "qmc_batch_plan_destroy": (None, [C.c_void_p]),
     "qmc_integrate": (C.c_int, [_P(qmc_integrand), _P(qmc_genvec_table), C.c_uint64, C.c_uint64,
                                 qmc_transform, _P(qmc_fit_opts), C.c_uint64, _P(qmc_options),
                                 C.c_void_p, _P(qmc_result)]),

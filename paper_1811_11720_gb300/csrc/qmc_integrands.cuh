@@ -35,8 +35,9 @@ struct FamilyShared {
     PolyShared poly;
 };
 
-template <int FAM>
-__device__ __forceinline__ void stage_family(const SumsParams &p, FamilyShared &fs) {
+// P: SumsParams or BatchItem (fields d, c, w, h, nu, nf, ucoef, fcoef, uexp, fexp, pa, pb, lam)
+template <int FAM, class P>
+__device__ __forceinline__ void stage_family(const P &p, FamilyShared &fs) {
     const int tid = threadIdx.x;
     if constexpr (FAM == QMC_SECTOR || FAM == QMC_FEYNMAN) {
         stage_poly(p, fs.poly);

@@ -47,4 +47,26 @@ struct SumsParams {
     unsigned long long *counters;     // [2] or nullptr
 };
 
+// One integral of a batch (qmc_batch_sums), built on the host and kept in the workspace.
+// Field names match SumsParams so the staging and per-stream code serve both kernels.
+struct BatchItem {
+    uint64_t n, i_begin, i_end;
+    uint64_t tile_begin, tiles;   // global index of the first tile, number of tiles
+    uint64_t partial_off;         // offset of this item's partials, in doubles
+    uint32_t L;                   // points per stream and tile
+    int d;
+    double cd;                    // Korobov C^d
+    DimConst dc[kMaxDim];
+    const uint64_t *shifts;       // [m][d]
+    TransformParams t;
+    const double *fit;            // [d][6] or nullptr
+    int family;
+    const double *c, *w;
+    const int64_t *h;
+    int nu, nf;
+    const double *ucoef, *fcoef;
+    const int32_t *uexp, *fexp;
+    double pa, pb, lam;
+};
+
 }  // namespace qmc

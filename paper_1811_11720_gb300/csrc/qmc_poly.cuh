@@ -43,7 +43,8 @@ __device__ __forceinline__ uint64_t pack_monomial(const int32_t *e, int d) {
     return code | (uint64_t)deg;
 }
 
-__device__ __forceinline__ void stage_poly(const SumsParams &p, PolyShared &ps) {
+template <class P>
+__device__ __forceinline__ void stage_poly(const P &p, PolyShared &ps) {
     const int tid = threadIdx.x;
     if (tid == 0) {
         ps.nu = p.nu;

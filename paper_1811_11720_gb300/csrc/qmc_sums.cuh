@@ -32,17 +32,11 @@ __device__ __forceinline__ void neumaier_add(double &s, double &c, double v) {
     s = t;
 }
 
-template <int FAM, int TK>
-__global__ void __launch_bounds__(kSumsThreads) sums_kernel(const __grid_constant__ SumsParams p) {
-    __shared__ FamilyShared fsh;
-    __shared__ double s_fit[kMaxDim * kFitStride];
-    __shared__ double s_red[2 * kSumsThreads];
-
+// Fit constants per dimension in shared memory (see apply_fit).
+__device__ __forceinline__ void prepare_fit(const double *fit, int d, double *s_fit) {
     const int tid = threadIdx.x;
-    stage_family<FAM>(p, fsh);
-    const bool use_fit = p.fit != nullptr;
-    if (use_fit && tid < p.d) {
-        const double *a = p.fit + 6 * tid;
+    if (fit && tid < d) {
+        const double *a = fit + 6 * tid;
         double a2 = fabs(a[2]), a3 = fabs(a[3]);
         double *o = s_fit + kFitStride * tid;
         o[0] = a[0];
@@ -55,18 +49,108 @@ __global__ void __launch_bounds__(kSumsThreads) sums_kernel(const __grid_constan
         o[7] = o[2] * a[0];
         o[8] = o[3] * a[1];
     }
+}
+
+// One stream of one shift: sum of g over points [i0, i0 + cnt) of the lattice described by
+// P (fields n, d, dc[], t).  Two-level FP64 accumulation: blocks of kInner samples, then
+// the block sums (rounding error ~ (kInner + L/kInner) ulp instead of L ulp).  The
+// per-thread lattice state lives in local memory (L1): the dimension loop is not unrolled,
+// which keeps the register count low; the FP64 pipe, not L1, bounds the kernel.
+template <int FAM, int TK, class P>
+__device__ __forceinline__ void stream_sums(const P &p, const FamilyShared &fsh, const double *s_fit,
+                                            bool use_fit, const uint64_t *dsh, double cd,
+                                            uint64_t i0, uint64_t cnt, double &acc_re,
+                                            double &acc_im, unsigned long long &nonfinite,
+                                            unsigned long long &signfail) {
+    const int d = p.d;
+    const uint64_t n = p.n;
+    double in_re = 0.0, in_im = 0.0;
+    acc_re = 0.0;
+    acc_im = 0.0;
+    if (!cnt) return;
+    uint64_t fhi[kMaxDim], flo[kMaxDim], rem[kMaxDim];
+#pragma unroll 1
+    for (int j = 0; j < d; ++j) lattice_state_at(i0, p.dc[j], n, fhi[j], flo[j], rem[j]);
+#pragma unroll 1
+    for (uint64_t t = 0; t < cnt; ++t) {
+        Weight W{1.0, 1.0, 1.0};
+        FamilyAcc<FAM> fa;
+        fa.init(fsh);
+#pragma unroll 1
+        for (int j = 0; j < d; ++j) {
+            double u = fixed_to_double(fhi[j] + dsh[j], flo[j], rem[j], n);
+            Mapped mx = apply_transform<TK>(u, p.t, W);
+            if (use_fit) mx = Mapped{apply_fit(reflected(mx), s_fit + kFitStride * j, W.w), false};
+            fa.add(j, mx, fsh);
+            lattice_step(p.dc[j], n, fhi[j], flo[j], rem[j]);
+        }
+        double wt = weight_finish<TK>(W, p.t, cd);
+        double g_re, g_im;
+        fa.finish(d, fsh, g_re, g_im, signfail);
+        g_re *= wt;
+        if constexpr (FamilyAcc<FAM>::kComplex) g_im *= wt;
+        if (not_finite(g_re) || (FamilyAcc<FAM>::kComplex && not_finite(g_im))) ++nonfinite;
+        in_re += g_re;
+        if constexpr (FamilyAcc<FAM>::kComplex) in_im += g_im;
+        if ((t & (kInner - 1)) == kInner - 1) {
+            acc_re += in_re;
+            in_re = 0.0;
+            if constexpr (FamilyAcc<FAM>::kComplex) {
+                acc_im += in_im;
+                in_im = 0.0;
+            }
+        }
+    }
+    acc_re += in_re;
+    if constexpr (FamilyAcc<FAM>::kComplex) acc_im += in_im;
+}
+
+// Per-shift tile partial: fixed-order compensated sum over the block's spb streams of
+// shift k, written as (sum, compensation) to out_re[2k..] (and out_im).  Contains the
+// block barriers; every thread of the block must call it.
+template <bool CPLX>
+__device__ __forceinline__ void tile_partial(double acc_re, double acc_im, double *s_red, int m,
+                                             int spb, int s_local, int k, bool active,
+                                             double *out_re, double *out_im) {
+    const int tid = threadIdx.x;
+    s_red[tid] = acc_re;
+    if constexpr (CPLX) s_red[kSumsThreads + tid] = acc_im;
+    __syncthreads();
+    if (s_local == 0 && active) {
+        double sr = 0.0, cr = 0.0, si = 0.0, ci = 0.0;
+        for (int s = 0; s < spb; ++s) {
+            neumaier_add(sr, cr, s_red[s * m + k]);
+            if constexpr (CPLX) neumaier_add(si, ci, s_red[kSumsThreads + s * m + k]);
+        }
+        out_re[2 * k] = sr;
+        out_re[2 * k + 1] = cr;
+        if constexpr (CPLX) {
+            out_im[2 * k] = si;
+            out_im[2 * k + 1] = ci;
+        }
+    }
+    __syncthreads();
+}
+
+template <int FAM, int TK>
+__global__ void __launch_bounds__(kSumsThreads) sums_kernel(const __grid_constant__ SumsParams p) {
+    __shared__ FamilyShared fsh;
+    __shared__ double s_fit[kMaxDim * kFitStride];
+    __shared__ double s_red[2 * kSumsThreads];
+    constexpr bool kCplx = FamilyAcc<FAM>::kComplex;
+
+    const int tid = threadIdx.x;
+    stage_family<FAM>(p, fsh);
+    prepare_fit(p.fit, p.d, s_fit);
     __syncthreads();
 
     const int m = p.m, d = p.d;
     const int k = tid % m;
     const int s_local = tid / m;
     const bool active = s_local < p.spb;
-    const uint64_t n = p.n;
     double cd = 1.0;  // Korobov C^d
     if constexpr (TK == QMC_T_KOROBOV) cd = ipow_u(p.t.C, d);
 
-    // per-thread state lives in local memory (L1): the dimension loop is not unrolled,
-    // which keeps the register count low; the FP64 pipe, not L1, bounds the kernel
     uint64_t dsh[kMaxDim];
 #pragma unroll 1
     for (int j = 0; j < d; ++j) dsh[j] = active ? (p.shifts[(size_t)k * d + j] << 11) : 0ull;
@@ -78,66 +162,12 @@ __global__ void __launch_bounds__(kSumsThreads) sums_kernel(const __grid_constan
         const uint64_t i0 = p.i_begin + tile * ptile + (uint64_t)s_local * p.L;
         uint64_t cnt = 0;
         if (active && i0 < p.i_end) cnt = (p.i_end - i0 < p.L) ? (p.i_end - i0) : p.L;
-        // two-level FP64 accumulation: blocks of kInner samples, then the block sums
-        // (rounding error ~ (kInner + L/kInner) ulp instead of L ulp)
-        double acc_re = 0.0, acc_im = 0.0, in_re = 0.0, in_im = 0.0;
-        if (cnt) {
-            uint64_t fhi[kMaxDim], flo[kMaxDim], rem[kMaxDim];
-#pragma unroll 1
-            for (int j = 0; j < d; ++j) lattice_state_at(i0, p.dc[j], n, fhi[j], flo[j], rem[j]);
-#pragma unroll 1
-            for (uint64_t t = 0; t < cnt; ++t) {
-                Weight W{1.0, 1.0, 1.0};
-                FamilyAcc<FAM> fa;
-                fa.init(fsh);
-#pragma unroll 1
-                for (int j = 0; j < d; ++j) {
-                    double u = fixed_to_double(fhi[j] + dsh[j], flo[j], rem[j], n);
-                    Mapped mx = apply_transform<TK>(u, p.t, W);
-                    if (use_fit) mx = Mapped{apply_fit(reflected(mx), s_fit + kFitStride * j, W.w), false};
-                    fa.add(j, mx, fsh);
-                    lattice_step(p.dc[j], n, fhi[j], flo[j], rem[j]);
-                }
-                double wt = weight_finish<TK>(W, p.t, cd);
-                double g_re, g_im;
-                fa.finish(d, fsh, g_re, g_im, signfail);
-                g_re *= wt;
-                if constexpr (FamilyAcc<FAM>::kComplex) g_im *= wt;
-                if (not_finite(g_re) || (FamilyAcc<FAM>::kComplex && not_finite(g_im))) ++nonfinite;
-                in_re += g_re;
-                if constexpr (FamilyAcc<FAM>::kComplex) in_im += g_im;
-                if ((t & (kInner - 1)) == kInner - 1) {
-                    acc_re += in_re;
-                    in_re = 0.0;
-                    if constexpr (FamilyAcc<FAM>::kComplex) {
-                        acc_im += in_im;
-                        in_im = 0.0;
-                    }
-                }
-            }
-            acc_re += in_re;
-            if constexpr (FamilyAcc<FAM>::kComplex) acc_im += in_im;
-        }
-        // per-shift tile partial: fixed-order compensated sum over the block's streams
-        s_red[tid] = acc_re;
-        if constexpr (FamilyAcc<FAM>::kComplex) s_red[kSumsThreads + tid] = acc_im;
-        __syncthreads();
-        if (s_local == 0 && active) {
-            double sr = 0.0, cr = 0.0, si = 0.0, ci = 0.0;
-            for (int s = 0; s < p.spb; ++s) {
-                neumaier_add(sr, cr, s_red[s * m + k]);
-                if constexpr (FamilyAcc<FAM>::kComplex) neumaier_add(si, ci, s_red[kSumsThreads + s * m + k]);
-            }
-            double *out = p.partials + 2 * (tile * (uint64_t)m + k);
-            out[0] = sr;
-            out[1] = cr;
-            if constexpr (FamilyAcc<FAM>::kComplex) {
-                double *oi = p.partials + 2 * (p.tiles * (uint64_t)m) + 2 * (tile * (uint64_t)m + k);
-                oi[0] = si;
-                oi[1] = ci;
-            }
-        }
-        __syncthreads();
+        double acc_re, acc_im;
+        stream_sums<FAM, TK>(p, fsh, s_fit, p.fit != nullptr, dsh, cd, i0, cnt, acc_re, acc_im,
+                             nonfinite, signfail);
+        double *out_re = p.partials + 2 * (tile * (uint64_t)m);
+        double *out_im = p.partials + 2 * (p.tiles * (uint64_t)m) + 2 * (tile * (uint64_t)m);
+        tile_partial<kCplx>(acc_re, acc_im, s_red, m, p.spb, s_local, k, active, out_re, out_im);
     }
     if (p.counters && (nonfinite | signfail)) {
         if (nonfinite) atomicAdd(p.counters, nonfinite);

@@ -357,8 +357,13 @@ def run_batch_workload(args):
     tb, ts = [], []
     for _ in range(args.steps):
         torch.cuda.synchronize()
-        ev[0].record(s); g_b.replay(); ev[1].record(s)
-        ev[2].record(s); g_s.replay(); ev[3].record(s)
+        with torch.cuda.stream(s):          # replay and events on the same stream
+            ev[0].record(s)
+            g_b.replay()
+            ev[1].record(s)
+            ev[2].record(s)
+            g_s.replay()
+            ev[3].record(s)
         torch.cuda.synchronize()
         tb.append(ev[0].elapsed_time(ev[1]))
         ts.append(ev[2].elapsed_time(ev[3]))

@@ -17,7 +17,7 @@ using namespace qmc::host;
 
 namespace {
 
-constexpr int kBatchRedThreads = 128;
+constexpr int kBatchRedThreads = 256;   // as the single-integral reduction: same fold order
 
 // dd helpers (fixed-order double-double folding of the tile partials)
 struct dd2 {

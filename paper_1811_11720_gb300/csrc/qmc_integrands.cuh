@@ -40,7 +40,7 @@ template <int FAM, class P>
 __device__ __forceinline__ void stage_family(const P &p, FamilyShared &fs) {
     const int tid = threadIdx.x;
     if constexpr (FAM == QMC_SECTOR || FAM == QMC_FEYNMAN) {
-        stage_poly(p, fs.poly);
+        stage_poly(p, fs.poly, FAM == QMC_SECTOR);
     } else {
         if (tid < p.d) {
             double c = p.c ? p.c[tid] : 0.0;

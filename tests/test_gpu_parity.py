@@ -262,12 +262,17 @@ def test_feynman_complex_matches_oracle(env):
     assert cnt[1] == o["signfail"]
 
 
-def test_sector_real_matches_oracle(env):
+@pytest.mark.parametrize("d,nu,nf", [(6, 40, 120), (3, 4, 5), (8, 400, 400), (16, 30, 600),
+                                     (8, 5, 400), (5, 300, 6)])
+def test_sector_real_matches_oracle(env, d, nu, nf):
+    """Dense multivariate Horner (many monomials, duplicates merged) and the sparse list
+    (few monomials) against the oracle's term-by-term sum."""
     q, torch, dev, tab = env
-    fl = W.sector_like(4, 6, 40, 120)
-    n, d, m = 4691, 6, 4
+    nf = min(nf, 512)
+    fl = W.sector_like(4 + d, d, nu, nf)
+    n, m = 4691, 4
     D = O.shifts(13, m, d)
-    z = tab.z_for(n)[:d]
+    z = tab.z_for(n)[:d] if d <= 10 else L.cbc_naive(n, d)[0]
     _, gre, _, _ = _gpu_sums(env, q.Integrand.polynomial(fl), n, z, D, ("korobov", 2))
     o = O.shift_sums(O.from_feynman(fl), ("korobov", 2), n, z, D)
     _compare(gre, None, o, n)

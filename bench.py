@@ -385,6 +385,96 @@ def run_batch_workload(args):
     print(json.dumps(line))
 
 
+def run_serve_workload(args):
+    """Serving: Poisson arrivals of config-3-like integrals (complex, d = 5, contour
+    deformation, Korobov-3, m = 32), each with a relative error target log-uniform in
+    [1e-8, 1e-3] and an evaluation budget; continuous batching (qmc_server) against the
+    same arrival stream served one integral at a time (qmc_integrate, adaptive).  Reports
+    p50/p99 latency (arrival to completion) and integrals/s for both."""
+    import torch
+
+    import paper_1811_11720_gb300 as q
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    table = q.GenvecTable.load()
+    rng = np.random.default_rng(args.seed)
+    N = args.requests
+    reqs = []
+    for i in range(N):
+        f = q.Integrand.polynomial(W.feynman_regular(args.seed + i))
+        eps = float(10 ** rng.uniform(-8, -3))
+        reqs.append((f, eps))
+    out = {"metric": "served integrals/s", "unit": "integrals/s", "higher_is_better": True,
+           "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "feynman_d5_korobov3_m32_eps1e-8..1e-3_poisson",
+                      "requests": N, "maxeval": args.serve_maxeval}, "rates": []}
+
+    def arrivals(rate):
+        r = np.random.default_rng(args.seed + int(rate * 1000))
+        return np.cumsum(r.exponential(1.0 / rate, N))
+
+    for rate in args.rates:
+        t_arr = arrivals(rate)
+        # continuous batching
+        srv = q.Server(table, memory_budget=int(args.serve_budget), max_slots=256, m=M_SHIFTS)
+        ids = [None] * N
+        done_t = [None] * N
+        t0 = time.perf_counter()
+        nxt = 0
+        open_ids = {}
+        while nxt < N or open_ids:
+            now = time.perf_counter() - t0
+            while nxt < N and t_arr[nxt] <= now:
+                f, eps = reqs[nxt]
+                ids[nxt] = srv.submit(f, epsrel=eps, epsabs=0.0, minn=1021,
+                                      maxeval=int(args.serve_maxeval), seed=nxt)
+                open_ids[ids[nxt]] = nxt
+                nxt += 1
+            if open_ids:
+                srv.step()
+                tnow = time.perf_counter() - t0
+                for rid in list(open_ids):
+                    if srv.status(rid)["state"] == srv.DONE:
+                        done_t[open_ids.pop(rid)] = tnow
+            elif nxt < N:
+                time.sleep(max(0.0, t_arr[nxt] - (time.perf_counter() - t0)))
+        span_b = max(done_t) - t_arr[0]
+        lat_b = np.array(done_t) - t_arr
+        met_b = sum(srv.status(ids[i])["err"] <= reqs[i][1] * abs(srv.status(ids[i])["integral"])
+                    for i in range(N))
+        res_b = [srv.status(ids[i]) for i in range(N)]
+        srv.close()
+        # one integral at a time, FIFO, same arrivals
+        done_s = [None] * N
+        t0 = time.perf_counter()
+        res_s = []
+        for i in range(N):
+            now = time.perf_counter() - t0
+            if t_arr[i] > now:
+                time.sleep(t_arr[i] - now)
+            f, eps = reqs[i]
+            r = q.integrate(f, table, 1021, M_SHIFTS, ("korobov", 3), seed=i,
+                            opts=q.options(epsrel=eps, epsabs=0.0, maxeval=int(args.serve_maxeval)))
+            done_s[i] = time.perf_counter() - t0
+            res_s.append(r)
+        span_s = max(done_s) - t_arr[0]
+        lat_s = np.array(done_s) - t_arr
+        same = all(rb["integral"] == rs["integral"] for rb, rs in zip(res_b, res_s))
+        out["rates"].append({
+            "rate_per_s": rate,
+            "batched": {"integrals_per_s": N / span_b, "p50_s": float(np.percentile(lat_b, 50)),
+                        "p99_s": float(np.percentile(lat_b, 99)), "goal_met": int(met_b)},
+            "one_at_a_time": {"integrals_per_s": N / span_s, "p50_s": float(np.percentile(lat_s, 50)),
+                              "p99_s": float(np.percentile(lat_s, 99))},
+            "same_results": bool(same)})
+    best = out["rates"][-1]
+    out["value"] = best["batched"]["integrals_per_s"]
+    out["p50_s"] = best["batched"]["p50_s"]
+    out["p99_s"] = best["batched"]["p99_s"]
+    print(json.dumps(out))
+
+
 def cpu_baseline(budget_s: float, items, nthreads: int | None = None):
     """The oracle as it stands on the host cores: per-shift sums over a bounded prefix of
     the same lattices, scaled to evaluations per second."""
@@ -426,12 +516,19 @@ def main():
     ap.add_argument("--no-kernel-events", dest="kernel_events", action="store_false")
     ap.add_argument("--only", default=None, help="FAMILY:D:TRANSFORM, e.g. 4:10:korobov3")
     ap.add_argument("--n", type=int, default=N_LATTICE, help="lattice size (a table size)")
-    ap.add_argument("--workload", default="genz", choices=["genz", "batch"])
+    ap.add_argument("--workload", default="genz", choices=["genz", "batch", "serve"])
+    ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--rates", type=float, nargs="*", default=[2.0, 8.0, 32.0])
+    ap.add_argument("--serve-maxeval", type=float, default=3.2e7)
+    ap.add_argument("--serve-budget", type=float, default=4e9)
     ap.add_argument("--batch-count", type=int, default=2000)
     ap.add_argument("--batch-nmax", type=float, default=1e5)
     args = ap.parse_args()
     if args.workload == "batch":
         run_batch_workload(args)
+        return
+    if args.workload == "serve":
+        run_serve_workload(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -291,6 +291,54 @@ int qmc_batch_autotune(const qmc_batch_item *items, int count, void *workspace,
                        size_t workspace_bytes, double *sums, void *stream,
                        qmc_batch_config *best);
 
+/* ---- serving: continuous batching of adaptive integrations ---------------------------- */
+
+/* A server owns a device memory pool of memory_budget bytes (one cudaMalloc at creation)
+ * and runs at most max_slots requests at a time, all with m shifts (2..256) and the given
+ * transform.  Requests are integrals with an error goal (epsrel, epsabs, the rule of the
+ * adaptive mode, Sec. 3.3.1, errormode all) and an evaluation budget maxeval, starting
+ * at get_next_n(minn).  Each qmc_server_step admits queued requests in arrival order
+ * while memory and slots allow (reserving coefficients, shifts and the tile partials of
+ * the request's largest admissible lattice), runs every admitted request on its current
+ * lattice in one batched launch per integrand family, and then completes requests whose
+ * goal is met or whose budget is spent, moving the others to larger table sizes.  A
+ * request's result does not depend on the other requests: it equals qmc_integrate with
+ * the same arguments as long as neither needs more shifts than m.
+ * Families: as for batches.  The server is not thread-safe across steps of one server
+ * from several threads (calls are serialised by a lock). */
+enum { QMC_REQ_PENDING = 0, QMC_REQ_ACTIVE = 1, QMC_REQ_DONE = 2 };
+typedef struct {
+    size_t memory_budget;
+    int max_slots;
+    uint64_t m;
+    qmc_transform transform;
+} qmc_server_config;
+typedef struct qmc_server qmc_server;
+
+/* table: host, copied.  stream: the server's CUDA stream (NULL = default).  Errors:
+ * QMC_ERR_ARG/M/TRANSFORM, QMC_ERR_WORKSPACE (budget below the fixed per-slot buffers),
+ * QMC_ERR_CUDA, QMC_ERR_NO_DEVICE. */
+int qmc_server_create(const qmc_genvec_table *table, const qmc_server_config *cfg,
+                      void *stream, qmc_server **out);
+void qmc_server_destroy(qmc_server *s);
+
+/* Queue a request; f has host arrays (copied).  *id receives its identifier. */
+int qmc_server_submit(qmc_server *s, const qmc_integrand *f, double epsrel, double epsabs,
+                      uint64_t minn, uint64_t maxeval, uint64_t seed, uint64_t *id);
+
+/* One scheduling round (synchronises the server's stream); *completed (may be NULL)
+ * receives the number of requests that finished in it. */
+int qmc_server_step(qmc_server *s, int *completed);
+
+/* State of a request (QMC_REQ_*), its result so far (final once done) and, when done, the
+ * seconds from submission to completion.  Returns the request's status once done
+ * (QMC_OK, QMC_ERR_NONFINITE, QMC_ERR_N when no table size fits), QMC_OK before. */
+int qmc_server_status(qmc_server *s, uint64_t id, int *state, qmc_result *result,
+                      double *latency_s);
+
+/* Queued and running requests and the free bytes of the pool. */
+int qmc_server_counts(qmc_server *s, int *pending, int *active, size_t *free_bytes);
+
 /* ---- host entry points -------------------------------------------------------------- */
 
 /* Fit the PolySingular map (Eq. (ISfit), |a2|, |a3| form of App. A.5) per dimension to

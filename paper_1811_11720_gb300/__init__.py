@@ -21,13 +21,13 @@ import numpy as np
 from . import _capi
 from ._capi import (FAMILY, QMC_MAX_DIM, STATUS, TRANSFORM, qmc_batch_config, qmc_batch_item,
                     qmc_fit_opts, qmc_genvec_table, qmc_integrand, qmc_options, qmc_result,
-                    qmc_rule, qmc_transform)
+                    qmc_rule, qmc_server_config, qmc_transform)
 
 __all__ = ["QMCError", "lib", "GenvecTable", "Integrand", "make_transform", "get_next_n",
            "make_shifts", "rule", "points", "sums_workspace_bytes", "sums", "sums_noalloc",
            "finalize",
            "evaluate", "histogram_workspace_bytes", "histogram", "fit_polysingular",
-           "integrate", "integrate_device", "Batch", "DEFAULT_TABLE"]
+           "integrate", "integrate_device", "Batch", "Server", "DEFAULT_TABLE"]
 
 DEFAULT_TABLE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                              "tables", "cbc_korobov_a2_s10.txt")
@@ -401,6 +401,69 @@ class BatchPlan:
     def close(self):
         if self.handle:
             lib().qmc_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------------------
+def _result_dict(res: qmc_result) -> dict:
+    return {"integral": complex(res.integral.re, res.integral.im),
+            "error": complex(res.error.re, res.error.im),
+            "value": res.integral.re, "err": res.error.re,
+            "n": res.n, "m": res.m, "iterations": res.iterations, "evaluations": res.evaluations,
+            "nonfinite": res.nonfinite, "signfail": res.signfail}
+
+
+class Server:
+    """Continuous-batching request loop (qmc_server_*)."""
+
+    PENDING, ACTIVE, DONE = 0, 1, 2
+
+    def __init__(self, table: GenvecTable, memory_budget: int, max_slots: int, m: int,
+                 transform=("korobov", 3), stream=None):
+        cfg = qmc_server_config(int(memory_budget), int(max_slots), int(m), make_transform(transform))
+        h = C.c_void_p()
+        _check(lib().qmc_server_create(C.byref(table.struct), C.byref(cfg), _stream(stream),
+                                       C.byref(h)), "server_create")
+        self.handle = h
+        self._table = table
+
+    def submit(self, f: Integrand, epsrel: float, epsabs: float = 0.0, minn: int = 1021,
+               maxeval: int = 10**8, seed: int = 0) -> int:
+        fs = f.host_struct()
+        rid = C.c_uint64()
+        _check(lib().qmc_server_submit(self.handle, C.byref(fs), float(epsrel), float(epsabs),
+                                       int(minn), int(maxeval), int(seed) & (2**64 - 1),
+                                       C.byref(rid)), "server_submit")
+        return int(rid.value)
+
+    def step(self) -> int:
+        done = C.c_int()
+        _check(lib().qmc_server_step(self.handle, C.byref(done)), "server_step")
+        return int(done.value)
+
+    def status(self, rid: int):
+        st, res, lat = C.c_int(), qmc_result(), C.c_double()
+        code = lib().qmc_server_status(self.handle, int(rid), C.byref(st), C.byref(res), C.byref(lat))
+        if code not in (0, _capi.QMC_ERR_NONFINITE):
+            raise QMCError(code, "server_status")
+        out = _result_dict(res)
+        out.update({"state": int(st.value), "latency_s": float(lat.value), "status": int(code)})
+        return out
+
+    def counts(self):
+        p, a, f = C.c_int(), C.c_int(), C.c_size_t()
+        _check(lib().qmc_server_counts(self.handle, C.byref(p), C.byref(a), C.byref(f)), "server_counts")
+        return int(p.value), int(a.value), int(f.value)
+
+    def close(self):
+        if self.handle:
+            lib().qmc_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

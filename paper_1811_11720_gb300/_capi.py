@@ -68,6 +68,11 @@ class qmc_batch_config(C.Structure):
     _fields_ = [("streams_per_block", C.c_int), ("points_per_stream", C.c_uint32)]
 
 
+class qmc_server_config(C.Structure):
+    _fields_ = [("memory_budget", C.c_size_t), ("max_slots", C.c_int), ("m", C.c_uint64),
+                ("transform", qmc_transform)]
+
+
 class qmc_fit_opts(C.Structure):
     _fields_ = [("enabled", C.c_int), ("evaluateminn", C.c_uint64), ("bins", C.c_int),
                 ("maxiter", C.c_int), ("xtol", C.c_double), ("gtol", C.c_double),
@@ -109,6 +114,15 @@ PROTOTYPES = {
                                         C.c_void_p, C.c_size_t, C.c_void_p, _P(C.c_void_p)]),
     "qmc_batch_plan_run": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "qmc_batch_plan_destroy": (None, [C.c_void_p]),
+    "qmc_server_create": (C.c_int, [_P(qmc_genvec_table), _P(qmc_server_config), C.c_void_p,
+                                    _P(C.c_void_p)]),
+    "qmc_server_destroy": (None, [C.c_void_p]),
+    "qmc_server_submit": (C.c_int, [C.c_void_p, _P(qmc_integrand), C.c_double, C.c_double,
+                                    C.c_uint64, C.c_uint64, C.c_uint64, _P(C.c_uint64)]),
+    "qmc_server_step": (C.c_int, [C.c_void_p, _P(C.c_int)]),
+    "qmc_server_status": (C.c_int, [C.c_void_p, C.c_uint64, _P(C.c_int), _P(qmc_result),
+                                    _P(C.c_double)]),
+    "qmc_server_counts": (C.c_int, [C.c_void_p, _P(C.c_int), _P(C.c_int), _P(C.c_size_t)]),
     "qmc_integrate": (C.c_int, [_P(qmc_integrand), _P(qmc_genvec_table), C.c_uint64, C.c_uint64,
                                 qmc_transform, _P(qmc_fit_opts), C.c_uint64, _P(qmc_options),
                                 C.c_void_p, _P(qmc_result)]),

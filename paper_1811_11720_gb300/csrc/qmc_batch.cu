@@ -15,7 +15,7 @@
 using namespace qmc;
 using namespace qmc::host;
 
-namespace {
+namespace qmc {
 
 constexpr int kBatchRedThreads = 256;   // as the single-integral reduction: same fold order
 
@@ -116,6 +116,19 @@ bool batch_family_supported(int fam) {
            fam == QMC_GENZ_GAUSSIAN || fam == QMC_SECTOR || fam == QMC_FEYNMAN;
 }
 
+cudaError_t launch_batch_reduce(const BatchItem *d_items, int count, int m, int cplx,
+                                const double *partials, double *sums, cudaStream_t s) {
+    const uint64_t blocks = (uint64_t)count * m * (cplx ? 2 : 1);
+    batch_reduce_kernel<<<(unsigned)blocks, kBatchRedThreads, 0, s>>>(d_items, m, cplx, partials, sums);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_finalize(const BatchItem *d_items, int count, int m, int cplx,
+                                  const double *sums, double *results, cudaStream_t s) {
+    batch_finalize_kernel<<<(count + 127) / 128, 128, 0, s>>>(d_items, count, m, cplx, sums, results);
+    return cudaGetLastError();
+}
+
 // C^d by the same left-to-right binary powering as the device code (ipow_u), so a batch
 // with the default launch shape reproduces qmc_sums bit for bit.
 double ipow_host(double x, int e) {
@@ -129,6 +142,52 @@ double ipow_host(double x, int e) {
     }
     return r;
 }
+
+int fill_batch_item(BatchItem &it, const qmc_batch_item &b, int m, int spb, uint32_t Lcfg, int fam) {
+    int st = check_integrand_shape(&b.f);
+    if (st) return st;
+    if ((st = check_rule(&b.rule))) return st;
+    if (b.f.family != fam || (int)b.rule.m != m) return QMC_ERR_ARG;
+    if (b.f.dim != b.rule.dim) return QMC_ERR_DIM;
+    if (b.i_end <= b.i_begin || b.i_end > b.rule.n) return QMC_ERR_RANGE;
+    const uint64_t range = b.i_end - b.i_begin;
+    uint32_t L = Lcfg;
+    if (L == 0) {
+        Geometry g = geometry(range, m);
+        L = (g.spb == spb) ? g.L : std::max<uint32_t>(32, (uint32_t)std::min<uint64_t>(8192, (range + (uint64_t)spb * kTargetTiles - 1) / ((uint64_t)spb * kTargetTiles)));
+    }
+    const uint64_t ptile = (uint64_t)spb * L;
+    std::memset(&it, 0, sizeof(it));
+    it.n = b.rule.n;
+    it.i_begin = b.i_begin;
+    it.i_end = b.i_end;
+    it.tiles = (range + ptile - 1) / ptile;
+    it.L = L;
+    it.d = b.rule.dim;
+    for (int j = 0; j < it.d; ++j) it.dc[j] = dim_const(b.rule.z[j] % b.rule.n, b.rule.n);
+    it.shifts = b.rule.shifts;
+    it.t = make_transform(b.rule.transform);
+    it.cd = (b.rule.transform.kind == QMC_T_KOROBOV) ? ipow_host(it.t.C, it.d) : 1.0;
+    it.fit = b.rule.fit;
+    it.family = fam;
+    it.c = b.f.c;
+    it.w = b.f.w;
+    it.h = b.f.h;
+    it.nu = b.f.nu;
+    it.nf = b.f.nf;
+    it.ucoef = b.f.ucoef;
+    it.fcoef = b.f.fcoef;
+    it.uexp = b.f.uexp;
+    it.fexp = b.f.fexp;
+    it.pa = b.f.pa;
+    it.pb = b.f.pb;
+    it.lam = b.f.lambda;
+    return QMC_OK;
+}
+
+}  // namespace qmc
+
+namespace {
 
 struct BatchPlan {
     std::vector<BatchItem> items;
@@ -157,52 +216,14 @@ int plan_batch(const qmc_batch_item *in, int count, const qmc_batch_config *cfg,
     P.tile_begin.resize(count + 1);
     uint64_t tiles = 0, poff = 0;
     for (int q = 0; q < count; ++q) {
-        const qmc_batch_item &b = in[q];
-        int st = check_integrand_shape(&b.f);
-        if (st) return st;
-        if ((st = check_rule(&b.rule))) return st;
-        if (b.f.family != fam || (int)b.rule.m != m) return QMC_ERR_ARG;
-        if (b.f.dim != b.rule.dim) return QMC_ERR_DIM;
-        if (b.i_end <= b.i_begin || b.i_end > b.rule.n) return QMC_ERR_RANGE;
-        const uint64_t range = b.i_end - b.i_begin;
-        uint32_t L = Lcfg;
-        if (L == 0) {
-            Geometry g = geometry(range, m);
-            L = (g.spb == spb) ? g.L : std::max<uint32_t>(32, (uint32_t)std::min<uint64_t>(8192, (range + (uint64_t)spb * kTargetTiles - 1) / ((uint64_t)spb * kTargetTiles)));
-        }
-        const uint64_t ptile = (uint64_t)spb * L;
-        const uint64_t nt = (range + ptile - 1) / ptile;
         BatchItem &it = P.items[q];
-        std::memset(&it, 0, sizeof(it));
-        it.n = b.rule.n;
-        it.i_begin = b.i_begin;
-        it.i_end = b.i_end;
+        int st = fill_batch_item(it, in[q], m, spb, Lcfg, fam);
+        if (st) return st;
         it.tile_begin = tiles;
-        it.tiles = nt;
         it.partial_off = poff;
-        it.L = L;
-        it.d = b.rule.dim;
-        for (int j = 0; j < it.d; ++j) it.dc[j] = dim_const(b.rule.z[j] % b.rule.n, b.rule.n);
-        it.shifts = b.rule.shifts;
-        it.t = make_transform(b.rule.transform);
-        it.cd = (b.rule.transform.kind == QMC_T_KOROBOV) ? ipow_host(it.t.C, it.d) : 1.0;
-        it.fit = b.rule.fit;
-        it.family = fam;
-        it.c = b.f.c;
-        it.w = b.f.w;
-        it.h = b.f.h;
-        it.nu = b.f.nu;
-        it.nf = b.f.nf;
-        it.ucoef = b.f.ucoef;
-        it.fcoef = b.f.fcoef;
-        it.uexp = b.f.uexp;
-        it.fexp = b.f.fexp;
-        it.pa = b.f.pa;
-        it.pb = b.f.pb;
-        it.lam = b.f.lambda;
         P.tile_begin[q] = tiles;
-        tiles += nt;
-        poff += nt * (uint64_t)m * 2 * (P.cplx ? 2 : 1);
+        tiles += it.tiles;
+        poff += it.tiles * (uint64_t)m * 2 * (P.cplx ? 2 : 1);
     }
     P.tile_begin[count] = tiles;
     P.total_tiles = tiles;
@@ -227,14 +248,11 @@ int launch_planned(const BatchPlan &P, int count, void *workspace, double *sums,
     double *d_part = (double *)(ws + P.off_partials);
     if (launch_batch(P.family, d_items, d_tb, count, P.total_tiles, P.m, P.spb, d_part, counters, s) != cudaSuccess)
         return QMC_ERR_CUDA;
-    const int per_item = P.m * (P.cplx ? 2 : 1);
-    const uint64_t blocks = (uint64_t)count * per_item;
-    batch_reduce_kernel<<<(unsigned)blocks, kBatchRedThreads, 0, s>>>(d_items, P.m, P.cplx, d_part, sums);
-    if (cudaGetLastError() != cudaSuccess) return QMC_ERR_CUDA;
+    if (launch_batch_reduce(d_items, count, P.m, P.cplx, d_part, sums, s) != cudaSuccess) return QMC_ERR_CUDA;
     if (results) {
         if (P.m < 2) return QMC_ERR_M;
-        batch_finalize_kernel<<<(count + 127) / 128, 128, 0, s>>>(d_items, count, P.m, P.cplx, sums, results);
-        if (cudaGetLastError() != cudaSuccess) return QMC_ERR_CUDA;
+        if (launch_batch_finalize(d_items, count, P.m, P.cplx, sums, results, s) != cudaSuccess)
+            return QMC_ERR_CUDA;
     }
     return QMC_OK;
 }

@@ -40,4 +40,16 @@ cudaError_t launch_histogram(const SumsParams &p, int bins, double *hist, double
 
 int sm_count();
 
+// Batch building blocks shared by qmc_batch_sums and the serving loop.  Item partial
+// offsets are relative to `partials`.
+int fill_batch_item(BatchItem &it, const qmc_batch_item &b, int m, int spb, uint32_t Lcfg, int fam);
+bool batch_family_supported(int fam);
+cudaError_t launch_batch(int family, const BatchItem *items, const uint64_t *tile_begin, int count,
+                         uint64_t tiles, int m, int spb, double *partials,
+                         unsigned long long *counters, cudaStream_t s);
+cudaError_t launch_batch_reduce(const BatchItem *d_items, int count, int m, int cplx,
+                                const double *partials, double *sums, cudaStream_t s);
+cudaError_t launch_batch_finalize(const BatchItem *d_items, int count, int m, int cplx,
+                                  const double *sums, double *results, cudaStream_t s);
+
 }  // namespace qmc

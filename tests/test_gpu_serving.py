@@ -1,0 +1,99 @@
+"""Serving loop (continuous batching of adaptive integrations) on the GPU."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    import paper_1811_11720_gb300 as q
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test run without a CUDA device")
+    from paper_1811_11720_gb300 import build
+    build.build()
+    q.lib()
+    return q, torch, q.GenvecTable.load()
+
+
+def _drain(srv, ids, max_steps=200):
+    for _ in range(max_steps):
+        if all(srv.status(i)["state"] == srv.DONE for i in ids):
+            return
+        srv.step()
+    raise AssertionError("requests did not complete")
+
+
+def _feyn(q, seed):
+    return q.Integrand.polynomial(W.feynman_regular(seed))
+
+
+def test_result_alone_equals_result_in_the_mix(env):
+    q, torch, tab = env
+    srv = q.Server(tab, memory_budget=256 << 20, max_slots=16, m=16)
+    a = srv.submit(_feyn(q, 1), epsrel=3e-2, maxeval=5_000_000, seed=7)
+    _drain(srv, [a])
+    alone = srv.status(a)
+    srv.close()
+    srv = q.Server(tab, memory_budget=256 << 20, max_slots=16, m=16)
+    ids = [srv.submit(_feyn(q, 10 + i), epsrel=10 ** -(1 + i % 3), maxeval=2_000_000, seed=i)
+           for i in range(3)]
+    c, w = W.genz_params(4, 6, 3)
+    ids.append(srv.submit(q.Integrand.genz(4, c, w), epsrel=1e-6, maxeval=20_000_000, seed=3))
+    srv.step()                                  # others already running when a arrives
+    a2 = srv.submit(_feyn(q, 1), epsrel=3e-2, maxeval=5_000_000, seed=7)
+    ids += [srv.submit(_feyn(q, 20 + i), epsrel=1e-2, maxeval=1_000_000, seed=20 + i) for i in range(2)]
+    _drain(srv, ids + [a2])
+    mixed = srv.status(a2)
+    srv.close()
+    for k in ("integral", "error", "n", "iterations", "evaluations"):
+        assert mixed[k] == alone[k], k
+
+
+def test_server_matches_adaptive_integrate(env):
+    q, torch, tab = env
+    c, w = W.genz_params(4, 5, 2)
+    f = q.Integrand.genz(4, c, w)
+    ref = q.integrate(f, tab, 1021, 16, ("korobov", 3), seed=5,
+                      opts=q.options(epsrel=1e-8, epsabs=0.0, maxeval=10 ** 10))
+    srv = q.Server(tab, memory_budget=256 << 20, max_slots=4, m=16)
+    rid = srv.submit(f, epsrel=1e-8, epsabs=0.0, minn=1021, maxeval=10 ** 10, seed=5)
+    _drain(srv, [rid])
+    got = srv.status(rid)
+    srv.close()
+    assert got["integral"] == ref["integral"] and got["error"] == ref["error"]
+    assert got["n"] == ref["n"] and got["iterations"] == ref["iterations"]
+
+
+def test_memory_budget_limits_concurrency(env):
+    q, torch, tab = env
+    # each request reserves ~0.45 MB (complex partials of its largest lattice, n = 108863,
+    # plus coefficients and shifts) and the fixed buffers take ~20 KB: two fit in 1 MB
+    srv = q.Server(tab, memory_budget=1_000_000, max_slots=8, m=32)
+    ids = [srv.submit(_feyn(q, 40 + i), epsrel=1e-2, maxeval=4_000_000, seed=i) for i in range(6)]
+    most = 0
+    for _ in range(300):
+        srv.step()
+        p, a, free = srv.counts()
+        most = max(most, a)
+        if all(srv.status(i)["state"] == srv.DONE for i in ids):
+            break
+    done = all(srv.status(i)["state"] == srv.DONE for i in ids)
+    srv.close()
+    assert done
+    assert most == 2
+
+
+def test_server_rejects_bad_arguments(env):
+    q, torch, tab = env
+    with pytest.raises(q.QMCError) as e:
+        q.Server(tab, memory_budget=1 << 24, max_slots=4, m=1)
+    assert e.value.code == -5
+    srv = q.Server(tab, memory_budget=1 << 24, max_slots=4, m=8)
+    with pytest.raises(q.QMCError):
+        srv.submit(q.Integrand.trig(np.array([0.5]), np.array([1]), np.array([0.1])), epsrel=1e-3)
+    srv.close()

@@ -108,6 +108,27 @@ def feynman_like(seed: int, d: int = 5, deg_u: int = 2, deg_f: int = 3,
     return FeynmanLike(Polynomial(cu, eu), Polynomial(cf, ef), a, b, lam, d)
 
 
+def feynman_regular(seed: int, d: int = 5, beta: float = 0.95, eps: float = 5e-4,
+                    a: float = 1.0, b: float = 2.5, lam: float = 0.5) -> FeynmanLike:
+    """Feynman-parameter-like integrand whose integral exists: U as in ``feynman_like``
+    (all degree-2 monomials, coefficients U(-1, 2)) and
+        F = 1 - beta sum_k x_k (1 - x_k) + eps sum_{|m| = 3} c_m x^m,  c_m ~ U(-1, 2),
+    which is positive on every face of the cube (for beta < 4/(d-1) and small eps) and
+    negative around the centre (beta > 4/d), so F changes sign inside and the contour
+    deformation, which vanishes on the faces, keeps F(z) away from zero."""
+    rng = _rng(seed * 7907 + d)
+    eu = all_monomials(d, 2)
+    cu = rng.uniform(-1.0, 2.0, eu.shape[0])
+    e3 = all_monomials(d, 3)
+    c3 = eps * rng.uniform(-1.0, 2.0, e3.shape[0])
+    e0 = np.zeros((1, d), np.int32)
+    e1 = np.eye(d, dtype=np.int32)
+    e2 = 2 * np.eye(d, dtype=np.int32)
+    ef = np.vstack([e0, e1, e2, e3]).astype(np.int32)
+    cf = np.concatenate([[1.0], -beta * np.ones(d), beta * np.ones(d), c3])
+    return FeynmanLike(Polynomial(cu, eu), Polynomial(cf, ef), a, b, lam, d)
+
+
 def sector_like(seed: int, d: int, nterms_u: int, nterms_f: int,
                 a: float = 1.0, b: float = 2.5) -> FeynmanLike:
     """Real sector-like integrand ``U^a / F^b`` with positive coefficients ``U(0,1)``:

@@ -17,11 +17,12 @@ namespace qmc {
 template <int FAM, int TK>
 __device__ __forceinline__ void batch_stream(const BatchItem &it, const FamilyShared &fsh,
                                              const double *s_fit, const uint64_t *dsh,
-                                             uint64_t i0, uint64_t cnt, double &acc_re,
-                                             double &acc_im, unsigned long long &nonfinite,
+                                             uint64_t i0, uint64_t cnt, WarpLattice *wl,
+                                             double &acc_re, double &acc_im,
+                                             unsigned long long &nonfinite,
                                              unsigned long long &signfail) {
-    stream_sums<FAM, TK>(it, fsh, s_fit, it.fit != nullptr, dsh, it.cd, i0, cnt, acc_re, acc_im,
-                         nonfinite, signfail);
+    stream_sums<FAM, TK>(it, fsh, s_fit, it.fit != nullptr, dsh, it.cd, i0, cnt, wl, acc_re,
+                         acc_im, nonfinite, signfail);
 }
 
 template <int FAM>
@@ -32,6 +33,7 @@ __global__ void __launch_bounds__(kSumsThreads)
     __shared__ FamilyShared fsh;
     __shared__ double s_fit[kMaxDim * kFitStride];
     __shared__ double s_red[2 * kSumsThreads];
+    __shared__ WarpLattice s_lat[kSumsThreads / 32];
     __shared__ BatchItem s_item;
     __shared__ int s_q;
     constexpr bool kCplx = FamilyAcc<FAM>::kComplex;
@@ -73,18 +75,22 @@ __global__ void __launch_bounds__(kSumsThreads)
         if (active && i0 < it.i_end) cnt = (it.i_end - i0 < it.L) ? (it.i_end - i0) : it.L;
         double acc_re = 0.0, acc_im = 0.0;
         unsigned long long nonfinite = 0, signfail = 0;
+        WarpLattice *wl = (m & 31) ? nullptr : &s_lat[tid >> 5];
         switch (it.t.kind) {
         case QMC_T_NONE:
-            batch_stream<FAM, QMC_T_NONE>(it, fsh, s_fit, dsh, i0, cnt, acc_re, acc_im, nonfinite, signfail);
+            batch_stream<FAM, QMC_T_NONE>(it, fsh, s_fit, dsh, i0, cnt, wl, acc_re, acc_im, nonfinite, signfail);
             break;
         case QMC_T_BAKER:
-            batch_stream<FAM, QMC_T_BAKER>(it, fsh, s_fit, dsh, i0, cnt, acc_re, acc_im, nonfinite, signfail);
+            batch_stream<FAM, QMC_T_BAKER>(it, fsh, s_fit, dsh, i0, cnt, wl, acc_re, acc_im, nonfinite, signfail);
             break;
         case QMC_T_KOROBOV:
-            batch_stream<FAM, QMC_T_KOROBOV>(it, fsh, s_fit, dsh, i0, cnt, acc_re, acc_im, nonfinite, signfail);
+            batch_stream<FAM, QMC_T_KOROBOV>(it, fsh, s_fit, dsh, i0, cnt, wl, acc_re, acc_im, nonfinite, signfail);
+            break;
+        case kTKorobovInt:
+            batch_stream<FAM, kTKorobovInt>(it, fsh, s_fit, dsh, i0, cnt, wl, acc_re, acc_im, nonfinite, signfail);
             break;
         default:
-            batch_stream<FAM, QMC_T_SIDI>(it, fsh, s_fit, dsh, i0, cnt, acc_re, acc_im, nonfinite, signfail);
+            batch_stream<FAM, QMC_T_SIDI>(it, fsh, s_fit, dsh, i0, cnt, wl, acc_re, acc_im, nonfinite, signfail);
             break;
         }
         double *base = partials + it.partial_off;

@@ -147,7 +147,7 @@ int qmc_sums(const qmc_integrand *f, const qmc_rule *rule, uint64_t i_begin, uin
         p.tiles = g.tiles;
         p.shifts = rule->shifts + k0 * rule->dim;
         p.partials = (double *)ws;
-        cudaError_t e = launch_sums_any(f->family, rule->transform.kind, dim3((unsigned)g.tiles),
+        cudaError_t e = launch_sums_any(f->family, p.t.kind, dim3((unsigned)g.tiles),
                                         dim3(g.threads), s, p);
         if (e != cudaSuccess) return QMC_ERR_CUDA;
         // sums layout: re pairs for all m, then im pairs for all m; group k0 writes its slice

@@ -12,12 +12,19 @@ constexpr int kMaxKorobov = 8;
 constexpr int kMaxSidi = 8;
 constexpr int kSumsThreads = 256;   // threads per block of the lattice-sum kernel
 
+// Internal transform kind: symmetric Korobov<r,r>, 1 <= r <= kMaxKorobovInt, evaluated in
+// integer fixed point (qmc_fixed.cuh).  The public kind stays QMC_T_KOROBOV.
+constexpr int kTKorobovInt = 4;
+constexpr int kMaxKorobovInt = 4;
+
 // Korobov<r0,r1> (Eq. (korobov)) as used by the kernels: for u <= 1/2,
 //   phi(u) = u^(r0+1) sum_k A[k] u^k,  A[k] = C (-1)^k binom(r1,k) / (r0+k+1), k <= r1,
 // and for u > 1/2 the reflection phi(u) = 1 - v^(r1+1) sum_k B[k] v^k with v = 1 - u
 // (B: r0 and r1 exchanged).  The weight is C u^r0 (1-u)^r1, C = (r0+r1+1) binom(r0+r1,r0).
 struct TransformParams {
     int kind, r0, r1, deg;        // deg = max(r0, r1): Horner length (zero-padded)
+    int kfix_F, kfix_pad;         // kTKorobovInt: fractional bits of the Horner scheme
+    long long kfix[kMaxKorobovInt + 1];   // kTKorobovInt: A_k 2^kfix_F (exact integers)
     double A[kMaxKorobov + 1];
     double B[kMaxKorobov + 1];
     double C;                     // Korobov constant, or Sidi (pi/2^r) Gamma(r+1)/Gamma((r+1)/2)^2

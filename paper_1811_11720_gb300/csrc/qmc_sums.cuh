@@ -51,58 +51,119 @@ __device__ __forceinline__ void prepare_fit(const double *fit, int d, double *s_
     }
 }
 
+// Per-warp lattice state for the warp-cooperative path: two buffers of d coordinates each
+// (the state at point t is written to buffer t & 1), in shared memory.
+struct WarpLattice {
+    uint64_t fhi[2][kMaxDim];
+    uint64_t flo[2][kMaxDim];
+    uint64_t rem[2][kMaxDim];
+};
+
+// One evaluation of g at the point whose coordinate j has lattice state (fhi(j), flo(j),
+// rem(j)); adds it to the two-level accumulator.
+template <int FAM, int TK, class P, class Hi, class Lo, class Rem>
+__device__ __forceinline__ void eval_point(const P &p, const FamilyShared &fsh, const double *s_fit,
+                                           bool use_fit, const uint64_t *dsh, double cd, Hi fhi,
+                                           Lo flo, Rem rem, double &g_re, double &g_im,
+                                           unsigned long long &signfail) {
+    Weight W{1.0, 1.0, 1.0, Fx{0x8000000000000000ull, 1}};
+    FamilyAcc<FAM> fa;
+    fa.init(fsh);
+#pragma unroll 1
+    for (int j = 0; j < p.d; ++j) {
+        Mapped mx;
+        if constexpr (TK == kTKorobovInt) {
+            mx = korobov_int_x(fhi(j) + dsh[j], p.t, W);
+        } else {
+            const double u = fixed_to_double(fhi(j) + dsh[j], flo(j), rem(j), p.n);
+            mx = apply_transform<TK>(u, p.t, W);
+        }
+        if (use_fit) mx = Mapped{apply_fit(reflected(mx), s_fit + kFitStride * j, W.w), false};
+        fa.add(j, mx, fsh);
+    }
+    const double wt = weight_finish<TK>(W, p.t, cd);
+    fa.finish(p.d, fsh, g_re, g_im, signfail);
+    g_re *= wt;
+    if constexpr (FamilyAcc<FAM>::kComplex) g_im *= wt;
+}
+
 // One stream of one shift: sum of g over points [i0, i0 + cnt) of the lattice described by
 // P (fields n, d, dc[], t).  Two-level FP64 accumulation: blocks of kInner samples, then
-// the block sums (rounding error ~ (kInner + L/kInner) ulp instead of L ulp).  The
-// per-thread lattice state lives in local memory (L1): the dimension loop is not unrolled,
-// which keeps the register count low; the FP64 pipe, not L1, bounds the kernel.
+// the block sums (rounding error ~ (kInner + L/kInner) ulp instead of L ulp).
+//
+// Lattice state.  When a warp's 32 lanes are 32 shifts of the same stream (m a multiple of
+// 32; wl != nullptr), the state is shared: lane j < d keeps coordinate j in registers,
+// computes its start point and steps it, and publishes it to the warp's shared buffer once
+// per point; every lane reads the d coordinates from there (broadcast loads).  That is one
+// lattice step per lane and point instead of d.  Otherwise each thread keeps all d
+// coordinates in local memory (L1) and steps them itself.
 template <int FAM, int TK, class P>
 __device__ __forceinline__ void stream_sums(const P &p, const FamilyShared &fsh, const double *s_fit,
                                             bool use_fit, const uint64_t *dsh, double cd,
-                                            uint64_t i0, uint64_t cnt, double &acc_re,
-                                            double &acc_im, unsigned long long &nonfinite,
+                                            uint64_t i0, uint64_t cnt, WarpLattice *wl,
+                                            double &acc_re, double &acc_im,
+                                            unsigned long long &nonfinite,
                                             unsigned long long &signfail) {
+    constexpr bool kCplx = FamilyAcc<FAM>::kComplex;
     const int d = p.d;
     const uint64_t n = p.n;
     double in_re = 0.0, in_im = 0.0;
     acc_re = 0.0;
     acc_im = 0.0;
     if (!cnt) return;
-    uint64_t fhi[kMaxDim], flo[kMaxDim], rem[kMaxDim];
-#pragma unroll 1
-    for (int j = 0; j < d; ++j) lattice_state_at(i0, p.dc[j], n, fhi[j], flo[j], rem[j]);
-#pragma unroll 1
-    for (uint64_t t = 0; t < cnt; ++t) {
-        Weight W{1.0, 1.0, 1.0};
-        FamilyAcc<FAM> fa;
-        fa.init(fsh);
-#pragma unroll 1
-        for (int j = 0; j < d; ++j) {
-            double u = fixed_to_double(fhi[j] + dsh[j], flo[j], rem[j], n);
-            Mapped mx = apply_transform<TK>(u, p.t, W);
-            if (use_fit) mx = Mapped{apply_fit(reflected(mx), s_fit + kFitStride * j, W.w), false};
-            fa.add(j, mx, fsh);
-            lattice_step(p.dc[j], n, fhi[j], flo[j], rem[j]);
-        }
-        double wt = weight_finish<TK>(W, p.t, cd);
-        double g_re, g_im;
-        fa.finish(d, fsh, g_re, g_im, signfail);
-        g_re *= wt;
-        if constexpr (FamilyAcc<FAM>::kComplex) g_im *= wt;
-        if (not_finite(g_re) || (FamilyAcc<FAM>::kComplex && not_finite(g_im))) ++nonfinite;
+    auto accumulate = [&](uint64_t t, double g_re, double g_im) {
+        if (not_finite(g_re) || (kCplx && not_finite(g_im))) ++nonfinite;
         in_re += g_re;
-        if constexpr (FamilyAcc<FAM>::kComplex) in_im += g_im;
+        if constexpr (kCplx) in_im += g_im;
         if ((t & (kInner - 1)) == kInner - 1) {
             acc_re += in_re;
             in_re = 0.0;
-            if constexpr (FamilyAcc<FAM>::kComplex) {
+            if constexpr (kCplx) {
                 acc_im += in_im;
                 in_im = 0.0;
             }
         }
+    };
+    if (wl) {
+        const int lane = threadIdx.x & 31;
+        uint64_t fh = 0, fl = 0, rm = 0;
+        if (lane < d) lattice_state_at(i0, p.dc[lane], n, fh, fl, rm);
+#pragma unroll 1
+        for (uint64_t t = 0; t < cnt; ++t) {
+            const int b = (int)(t & 1);
+            if (lane < d) {
+                wl->fhi[b][lane] = fh;
+                if constexpr (TK != kTKorobovInt) {
+                    wl->flo[b][lane] = fl;
+                    wl->rem[b][lane] = rm;
+                }
+            }
+            __syncwarp();
+            double g_re, g_im = 0.0;
+            eval_point<FAM, TK>(
+                p, fsh, s_fit, use_fit, dsh, cd, [&](int j) { return wl->fhi[b][j]; },
+                [&](int j) { return wl->flo[b][j]; }, [&](int j) { return wl->rem[b][j]; }, g_re,
+                g_im, signfail);
+            accumulate(t, g_re, g_im);
+            if (lane < d) lattice_step(p.dc[lane], n, fh, fl, rm);
+        }
+    } else {
+        uint64_t fhi[kMaxDim], flo[kMaxDim], rem[kMaxDim];
+#pragma unroll 1
+        for (int j = 0; j < d; ++j) lattice_state_at(i0, p.dc[j], n, fhi[j], flo[j], rem[j]);
+#pragma unroll 1
+        for (uint64_t t = 0; t < cnt; ++t) {
+            double g_re, g_im = 0.0;
+            eval_point<FAM, TK>(
+                p, fsh, s_fit, use_fit, dsh, cd, [&](int j) { return fhi[j]; },
+                [&](int j) { return flo[j]; }, [&](int j) { return rem[j]; }, g_re, g_im, signfail);
+            accumulate(t, g_re, g_im);
+#pragma unroll 1
+            for (int j = 0; j < d; ++j) lattice_step(p.dc[j], n, fhi[j], flo[j], rem[j]);
+        }
     }
     acc_re += in_re;
-    if constexpr (FamilyAcc<FAM>::kComplex) acc_im += in_im;
+    if constexpr (kCplx) acc_im += in_im;
 }
 
 // Per-shift tile partial: fixed-order compensated sum over the block's spb streams of
@@ -137,6 +198,7 @@ __global__ void __launch_bounds__(kSumsThreads) sums_kernel(const __grid_constan
     __shared__ FamilyShared fsh;
     __shared__ double s_fit[kMaxDim * kFitStride];
     __shared__ double s_red[2 * kSumsThreads];
+    __shared__ WarpLattice s_lat[kSumsThreads / 32];
     constexpr bool kCplx = FamilyAcc<FAM>::kComplex;
 
     const int tid = threadIdx.x;
@@ -149,7 +211,7 @@ __global__ void __launch_bounds__(kSumsThreads) sums_kernel(const __grid_constan
     const int s_local = tid / m;
     const bool active = s_local < p.spb;
     double cd = 1.0;  // Korobov C^d
-    if constexpr (TK == QMC_T_KOROBOV) cd = ipow_u(p.t.C, d);
+    if constexpr (TK == QMC_T_KOROBOV || TK == kTKorobovInt) cd = ipow_u(p.t.C, d);
 
     uint64_t dsh[kMaxDim];
 #pragma unroll 1
@@ -163,8 +225,9 @@ __global__ void __launch_bounds__(kSumsThreads) sums_kernel(const __grid_constan
         uint64_t cnt = 0;
         if (active && i0 < p.i_end) cnt = (p.i_end - i0 < p.L) ? (p.i_end - i0) : p.L;
         double acc_re, acc_im;
-        stream_sums<FAM, TK>(p, fsh, s_fit, p.fit != nullptr, dsh, cd, i0, cnt, acc_re, acc_im,
-                             nonfinite, signfail);
+        stream_sums<FAM, TK>(p, fsh, s_fit, p.fit != nullptr, dsh, cd, i0, cnt,
+                             (m & 31) ? nullptr : &s_lat[tid >> 5], acc_re, acc_im, nonfinite,
+                             signfail);
         double *out_re = p.partials + 2 * (tile * (uint64_t)m);
         double *out_im = p.partials + 2 * (p.tiles * (uint64_t)m) + 2 * (tile * (uint64_t)m);
         tile_partial<kCplx>(acc_re, acc_im, s_red, m, p.spb, s_local, k, active, out_re, out_im);

@@ -14,6 +14,7 @@
 #pragma once
 #include <cstdint>
 
+#include "qmc_fixed.cuh"
 #include "qmc_fp.cuh"
 #include "qmc_params.cuh"
 
@@ -24,8 +25,10 @@ namespace qmc {
 //    t_j = v_j (1 - v_j) (one fused multiply-add) and raised to r once per evaluation.
 //  * Korobov<r0,r1>: prod u_j and prod (1 - u_j), raised to r0 and r1 once.
 //  * w: other factors (fit Jacobian, Sidi weights).
+//  * wp: integer-pipe Korobov<r,r>, prod_j t_j as a normalized Fx.
 struct Weight {
     double wu, w1, w;
+    Fx wp;
 };
 
 struct Mapped {
@@ -59,7 +62,8 @@ __device__ __forceinline__ Mapped apply_transform(double u, const TransformParam
             W.w1 *= lo ? w1v : v;             // 1 - u
         }
         return {y, !lo};
-    } else {  // QMC_T_SIDI
+    } else {
+        static_assert(TK == QMC_T_SIDI, "kTKorobovInt is evaluated by korobov_int_x");
         // phi = cr I_r(u), I_r = base I_(r mod 2) - (cos(pi u)/pi) sum_q a_q sin^(r-1-2q)
         double s, c;
         sincospi(u, &s, &c);
@@ -81,6 +85,13 @@ __device__ __forceinline__ Mapped apply_transform(double u, const TransformParam
     }
 }
 
+// The integer-pipe Korobov<r,r> (kTKorobovInt) takes the lattice state's top word
+// X = x 2^64 instead of the rounded u: v = min(x, 1 - x) in 0.64 fixed point.
+__device__ __forceinline__ Mapped korobov_int_x(uint64_t X, const TransformParams &t, Weight &W) {
+    const bool lo = !(X >> 63);
+    return {korobov_int(lo ? X : ~X, t, W.wp), !lo};
+}
+
 // cd = C^d for Korobov (folded once per launch).
 template <int TK>
 __device__ __forceinline__ double weight_finish(const Weight &W, const TransformParams &t,
@@ -88,6 +99,8 @@ __device__ __forceinline__ double weight_finish(const Weight &W, const Transform
     if constexpr (TK == QMC_T_KOROBOV) {
         if (t.r0 == t.r1) return cd * ipow_u(W.wu, t.r0) * W.w;
         return cd * ipow_u(W.wu, t.r0) * ipow_u(W.w1, t.r1) * W.w;
+    } else if constexpr (TK == kTKorobovInt) {
+        return korobov_int_weight(W.wp, t.r0, fx_of_double(cd)) * W.w;
     } else {
         return W.w;
     }

@@ -121,7 +121,11 @@ GENZ_CASES = [(fam, d, tr) for fam in (1, 2, 3, 4) for d in (2, 6, 10)
              [(1, 8, ("korobov", 1)), (4, 8, ("korobov", 2)), (3, 6, ("korobov", 4)),
               (2, 4, ("none",)), (5, 5, ("korobov", 3)), (6, 4, ("baker",)),
               (2, 3, ("sidi", 2)), (1, 3, ("sidi", 3)), (4, 5, ("korobov", 2, 5)),
-              (2, 16, ("baker",)), (3, 1, ("korobov", 3))]
+              (2, 16, ("baker",)), (3, 1, ("korobov", 3)),
+              # symmetric r <= 4 runs in integer fixed point; r = 0, r >= 5 and r0 != r1
+              # keep the FP64 Horner form
+              (1, 10, ("korobov", 4)), (4, 16, ("korobov", 3)), (3, 4, ("korobov", 0)),
+              (4, 6, ("korobov", 5)), (1, 3, ("korobov", 8)), (3, 5, ("korobov", 3, 1))]
 
 
 @pytest.mark.parametrize("fam,d,tr", GENZ_CASES)

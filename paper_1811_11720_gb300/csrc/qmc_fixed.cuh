@@ -67,9 +67,17 @@ __device__ __forceinline__ double fx_to_double(Fx a) {
     return __longlong_as_double((long long)(((uint64_t)be << 52) + mant));
 }
 
-// phi(v) for v = min(x, 1 - x), and the weight factor t = v (1 - v) folded into Wp (a
-// normalized running product).  V = v 2^64 in 0.64 fixed point (V <= 2^63).
-__device__ __forceinline__ double korobov_int(uint64_t V, const TransformParams &t, Fx &Wp) {
+// 0.64 fixed point of a value in [0, 1): floor(value 2^64).
+__device__ __forceinline__ uint64_t fx_to_fixed(Fx a) {
+    a = fx_norm(a);
+    const int sh = -a.e;   // >= 0 for values below 1
+    return sh < 64 ? (a.m >> sh) : 0ull;
+}
+
+// phi(v) for v = min(x, 1 - x) as Fx (mantissa >= 2^58), and the weight factor
+// t = v (1 - v) folded into Wp (a normalized running product).  V = v 2^64 in 0.64 fixed
+// point (V <= 2^63).
+__device__ __forceinline__ Fx korobov_int_phi(uint64_t V, const TransformParams &t, Fx &Wp) {
     const int r = t.r0;
     const int lz = __clzll(V);   // 64 for V == 0
     const Fx fv = {V ? (V << (lz & 63)) : 0ull, -lz};
@@ -93,7 +101,11 @@ __device__ __forceinline__ double korobov_int(uint64_t V, const TransformParams 
     }
     // t = v (1 - v), with 1 - v ~ (2^64 - 1 - V) 2^-64 (error <= 2^-63 relative)
     Wp = fx_norm(fx_mul(Wp, fx_mul(fv, Fx{~V, 0})));
-    return fx_to_double(fx_mul(pw, P));
+    return fx_mul(pw, P);
+}
+
+__device__ __forceinline__ double korobov_int(uint64_t V, const TransformParams &t, Fx &Wp) {
+    return fx_to_double(korobov_int_phi(V, t, Wp));
 }
 
 // C^d (prod_j t_j)^r rounded to double; cdx = C^d as Fx.

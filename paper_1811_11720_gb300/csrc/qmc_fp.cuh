@@ -8,9 +8,6 @@ namespace qmc {
 __device__ __forceinline__ bool le_half(double u) {
     return (unsigned long long)__double_as_longlong(u) <= 0x3FE0000000000000ull;
 }
-__device__ __forceinline__ bool gt_nonneg(double a, double b) {  // a > b for a, b >= 0
-    return (unsigned long long)__double_as_longlong(a) > (unsigned long long)__double_as_longlong(b);
-}
 
 // 1 - u for u in [1/2, 1], exact (Sterbenz), on the integer pipe.
 __device__ __forceinline__ double one_minus_upper(double u) {

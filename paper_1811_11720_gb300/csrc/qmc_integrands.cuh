@@ -23,6 +23,24 @@
 
 namespace qmc {
 
+// Fixed-point constants of the separable Genz families 1 and 3-6, whose linear and
+// quadratic forms run on the integer pipe when the coordinate arrives in 0.64 fixed point:
+//   linear (1, 3, 5, 6): cl_j = c_j 2^S with S = 62 - floor(log2 sum_j c_j), so every
+//     partial sum of c_j x_j (or c_j |x_j - w_j|) stays below 2^63;
+//   Gaussian (4): cq_j = c_j 2^S with S = 61 - floor(log2 max_j c_j), so |c_j (x_j - w_j)|
+//     2^S < 2^62 and each square (2^(2S - 64) scale) is below 2^60.
+// Each term truncates by at most one unit (2^-S, or 2^(64 - 2S) for squares); the forms
+// are therefore exact to ~2^-56 absolutely for the benchmark's c (||c||_1 <= 18).  ok is
+// false (double path) unless every c_j >= 0 and 0 <= w_j <= 1.
+struct FixedForms {
+    uint64_t cl[kMaxDim];
+    int64_t cq[kMaxDim];
+    int64_t w63[kMaxDim];    // w_j 2^63, at most 2^63 - 1
+    uint64_t w64[kMaxDim];   // w_j 2^64, at most 2^64 - 1
+    int S;
+    bool ok;
+};
+
 struct FamilyShared {
     double c[kMaxDim], w[kMaxDim], aux[kMaxDim];
     double mcw[kMaxDim];    // -c w
@@ -32,8 +50,53 @@ struct FamilyShared {
     double sub_hi[256];     // the same for j = 8 + bit
     double s0;
     int64_t h[kMaxDim];
+    FixedForms fx;
     PolyShared poly;
 };
+
+template <int FAM>
+constexpr bool kHasFixedForm = FAM == QMC_GENZ_OSCILLATORY || FAM == QMC_GENZ_CORNER_PEAK ||
+                               FAM == QMC_GENZ_GAUSSIAN || FAM == QMC_GENZ_C0 ||
+                               FAM == QMC_GENZ_DISCONTINUOUS;
+
+// v 2^-S for an integer v < 2^64, rounded once (the power of two is exact; v 2^-S is normal).
+__device__ __forceinline__ double scaled_fixed(uint64_t v, int S) {
+    const long long b = __double_as_longlong(__ull2double_rn(v));
+    return __longlong_as_double(b ? b - ((long long)S << 52) : 0ll);
+}
+
+// Per-thread staging of the fixed-point constants (threads tid < d; thread 0 writes S, ok).
+template <int FAM, class P>
+__device__ __forceinline__ void stage_fixed_forms(const P &p, FixedForms &fx) {
+    const int tid = threadIdx.x;
+    if (tid >= p.d) return;
+    double csum = 0.0, cmax = 0.0;
+    bool ok = p.c != nullptr && (p.w != nullptr || FAM == QMC_GENZ_OSCILLATORY ||
+                                 FAM == QMC_GENZ_CORNER_PEAK);
+    for (int i = 0; ok && i < p.d; ++i) {
+        const double c = p.c[i];
+        const double w = p.w ? p.w[i] : 0.0;
+        ok = c >= 0.0 && w >= 0.0 && w <= 1.0;
+        csum += c;
+        cmax = fmax(cmax, c);
+    }
+    int S;
+    if constexpr (FAM == QMC_GENZ_GAUSSIAN) S = cmax > 0.0 ? 61 - ilogb(cmax) : 61;
+    else S = csum > 0.0 ? 62 - ilogb(csum) : 62;
+    ok = ok && S >= 1 && S <= 120;
+    if (ok) {
+        const double c = p.c[tid];
+        const double w = p.w ? p.w[tid] : 0.0;
+        fx.cl[tid] = __double2ull_rz(ldexp(c, S));
+        fx.cq[tid] = __double2ll_rz(ldexp(c, S));
+        fx.w63[tid] = w >= 1.0 ? 0x7FFFFFFFFFFFFFFFll : __double2ll_rz(ldexp(w, 63));
+        fx.w64[tid] = w >= 1.0 ? 0xFFFFFFFFFFFFFFFFull : __double2ull_rz(ldexp(w, 64));
+    }
+    if (tid == 0) {
+        fx.S = S;
+        fx.ok = ok;
+    }
+}
 
 // P: SumsParams or BatchItem (fields d, c, w, h, nu, nf, ucoef, fcoef, uexp, fexp, pa, pb, lam)
 template <int FAM, class P>
@@ -68,6 +131,7 @@ __device__ __forceinline__ void stage_family(const P &p, FamilyShared &fs) {
                 fs.sub_hi[b] = hi;
             }
         }
+        if constexpr (kHasFixedForm<FAM>) stage_fixed_forms<FAM>(p, fs.fx);
     }
 }
 
@@ -95,6 +159,17 @@ struct FamilyAcc<QMC_GENZ_OSCILLATORY> {
     __device__ __forceinline__ void finish(int d, const FamilyShared &fs, double &re, double &im,
                                            unsigned long long &) {
         re = cos(mask ? s + reflected_c_sum(mask, d, fs) : s);
+        im = 0.0;
+    }
+    // fixed point: sum c_j x_j on the integer pipe
+    uint64_t sl;
+    __device__ __forceinline__ void init_fixed() { sl = 0; }
+    __device__ __forceinline__ void add_fixed(int j, uint64_t x, const FamilyShared &fs) {
+        sl += __umul64hi(x, fs.fx.cl[j]);
+    }
+    __device__ __forceinline__ void finish_fixed(int, const FamilyShared &fs, double &re,
+                                                 double &im, unsigned long long &) {
+        re = cos(fs.s0 + scaled_fixed(sl, fs.fx.S));
         im = 0.0;
     }
 };
@@ -134,6 +209,16 @@ struct FamilyAcc<QMC_GENZ_CORNER_PEAK> {
         re = 1.0 / ipow_u(t, d + 1);
         im = 0.0;
     }
+    uint64_t sl;
+    __device__ __forceinline__ void init_fixed() { sl = 0; }
+    __device__ __forceinline__ void add_fixed(int j, uint64_t x, const FamilyShared &fs) {
+        sl += __umul64hi(x, fs.fx.cl[j]);
+    }
+    __device__ __forceinline__ void finish_fixed(int d, const FamilyShared &fs, double &re,
+                                                 double &im, unsigned long long &) {
+        re = 1.0 / ipow_u(1.0 + scaled_fixed(sl, fs.fx.S), d + 1);
+        im = 0.0;
+    }
 };
 
 // 4: exp(-sum c_i^2 (x_i - w_i)^2)
@@ -150,6 +235,19 @@ struct FamilyAcc<QMC_GENZ_GAUSSIAN> {
     __device__ __forceinline__ void finish(int, const FamilyShared &, double &re, double &im,
                                            unsigned long long &) {
         re = exp(-s);
+        im = 0.0;
+    }
+    // fixed point: q = c (x - w) 2^S (|q| < 2^62), q^2 2^(2S - 64) < 2^60, summed in 64 bits
+    uint64_t sq;
+    __device__ __forceinline__ void init_fixed() { sq = 0; }
+    __device__ __forceinline__ void add_fixed(int j, uint64_t x, const FamilyShared &fs) {
+        const long long diff = (long long)(x >> 1) - fs.fx.w63[j];      // (x - w) 2^63
+        const long long q = __mul64hi(diff, fs.fx.cq[j]) * 2;           // c (x - w) 2^S
+        sq += (uint64_t)__mul64hi(q, q);
+    }
+    __device__ __forceinline__ void finish_fixed(int, const FamilyShared &fs, double &re,
+                                                 double &im, unsigned long long &) {
+        re = exp(-scaled_fixed(sq, 2 * fs.fx.S - 64));
         im = 0.0;
     }
 };
@@ -169,6 +267,18 @@ struct FamilyAcc<QMC_GENZ_C0> {
         re = exp(-s);
         im = 0.0;
     }
+    uint64_t sl;
+    __device__ __forceinline__ void init_fixed() { sl = 0; }
+    __device__ __forceinline__ void add_fixed(int j, uint64_t x, const FamilyShared &fs) {
+        const long long diff = (long long)(x >> 1) - fs.fx.w63[j];      // (x - w) 2^63
+        const uint64_t a = (uint64_t)(diff < 0 ? -diff : diff) << 1;    // |x - w| 2^64
+        sl += __umul64hi(a, fs.fx.cl[j]);
+    }
+    __device__ __forceinline__ void finish_fixed(int, const FamilyShared &fs, double &re,
+                                                 double &im, unsigned long long &) {
+        re = exp(-scaled_fixed(sl, fs.fx.S));
+        im = 0.0;
+    }
 };
 
 // 6: 0 if x_1 > w_1 or x_2 > w_2, else exp(sum c_i x_i)
@@ -180,14 +290,26 @@ struct FamilyAcc<QMC_GENZ_DISCONTINUOUS> {
     bool zero;
     __device__ __forceinline__ void init(const FamilyShared &) { s = 0.0; mask = 0; zero = false; }
     __device__ __forceinline__ void add(int j, const Mapped &m, const FamilyShared &fs) {
-        // x > w is y > w, or (1 - y > w, i.e. y < 1 - w) when reflected
-        if (j < 2) zero |= m.refl ? gt_nonneg(fs.w1[j], m.y) : gt_nonneg(m.y, fs.w[j]);
+        // x > w is y > w, or (1 - y > w, i.e. y < 1 - w) when reflected; w may lie outside
+        // [0, 1] here (the fixed-point form covers 0 <= w <= 1), so compare as doubles
+        if (j < 2) zero |= m.refl ? (fs.w1[j] > m.y) : (m.y > fs.w[j]);
         s = fma(m.refl ? -fs.c[j] : fs.c[j], m.y, s);
         mask |= (uint32_t)m.refl << j;
     }
     __device__ __forceinline__ void finish(int d, const FamilyShared &fs, double &re, double &im,
                                            unsigned long long &) {
         re = zero ? 0.0 : exp(mask ? s + reflected_c_sum(mask, d, fs) : s);
+        im = 0.0;
+    }
+    uint64_t sl;
+    __device__ __forceinline__ void init_fixed() { sl = 0; zero = false; }
+    __device__ __forceinline__ void add_fixed(int j, uint64_t x, const FamilyShared &fs) {
+        if (j < 2) zero |= x > fs.fx.w64[j];
+        sl += __umul64hi(x, fs.fx.cl[j]);
+    }
+    __device__ __forceinline__ void finish_fixed(int, const FamilyShared &fs, double &re,
+                                                 double &im, unsigned long long &) {
+        re = zero ? 0.0 : exp(scaled_fixed(sl, fs.fx.S));
         im = 0.0;
     }
 };

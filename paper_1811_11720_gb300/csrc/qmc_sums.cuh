@@ -68,6 +68,19 @@ __device__ __forceinline__ void eval_point(const P &p, const FamilyShared &fsh, 
                                            unsigned long long &signfail) {
     Weight W{1.0, 1.0, 1.0, Fx{0x8000000000000000ull, 1}};
     FamilyAcc<FAM> fa;
+    if constexpr (kFixedTransform<TK> && kHasFixedForm<FAM>) {
+        // coordinate and integrand form entirely in fixed point (no fit: the fit map
+        // needs x as a double)
+        if (!use_fit && fsh.fx.ok) {
+            fa.init_fixed();
+#pragma unroll 1
+            for (int j = 0; j < p.d; ++j) fa.add_fixed(j, transform_fixed<TK>(fhi(j) + dsh[j], p.t, W), fsh);
+            const double wt = weight_finish<TK>(W, p.t, cd);
+            fa.finish_fixed(p.d, fsh, g_re, g_im, signfail);
+            g_re *= wt;
+            return;
+        }
+    }
     fa.init(fsh);
 #pragma unroll 1
     for (int j = 0; j < p.d; ++j) {

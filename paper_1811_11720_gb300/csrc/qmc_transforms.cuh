@@ -92,6 +92,27 @@ __device__ __forceinline__ Mapped korobov_int_x(uint64_t X, const TransformParam
     return {korobov_int(lo ? X : ~X, t, W.wp), !lo};
 }
 
+// Transforms that are exact or fixed-point on the integer pipe can hand the integrand the
+// coordinate itself in 0.64 fixed point, x 2^64 (truncated), when the integrand takes it
+// (FamilyAcc::add_fixed): none (x is the shifted lattice fraction), baker (2 min(x, 1 - x))
+// and the integer Korobov (phi, or 1 - phi when reflected).
+template <int TK>
+constexpr bool kFixedTransform = TK == QMC_T_NONE || TK == QMC_T_BAKER || TK == kTKorobovInt;
+
+template <int TK>
+__device__ __forceinline__ uint64_t transform_fixed(uint64_t X, const TransformParams &t, Weight &W) {
+    if constexpr (TK == QMC_T_NONE) {
+        return X;
+    } else if constexpr (TK == QMC_T_BAKER) {
+        return ((X >> 63) ? ~X : X) << 1;   // min(X, 2^64 - 1 - X) < 2^63
+    } else {
+        static_assert(TK == kTKorobovInt, "no fixed-point form");
+        const bool lo = !(X >> 63);
+        const uint64_t F = fx_to_fixed(korobov_int_phi(lo ? X : ~X, t, W.wp));
+        return lo ? F : ~F;
+    }
+}
+
 // cd = C^d for Korobov (folded once per launch).
 template <int TK>
 __device__ __forceinline__ double weight_finish(const Weight &W, const TransformParams &t,

@@ -125,7 +125,10 @@ GENZ_CASES = [(fam, d, tr) for fam in (1, 2, 3, 4) for d in (2, 6, 10)
               # symmetric r <= 4 runs in integer fixed point; r = 0, r >= 5 and r0 != r1
               # keep the FP64 Horner form
               (1, 10, ("korobov", 4)), (4, 16, ("korobov", 3)), (3, 4, ("korobov", 0)),
-              (4, 6, ("korobov", 5)), (1, 3, ("korobov", 8)), (3, 5, ("korobov", 3, 1))]
+              (4, 6, ("korobov", 5)), (1, 3, ("korobov", 8)), (3, 5, ("korobov", 3, 1)),
+              # families 1 and 3-6 take x in fixed point under none, baker and Korobov r <= 4
+              (1, 5, ("none",)), (4, 7, ("none",)), (5, 8, ("baker",)), (6, 6, ("korobov", 2)),
+              (3, 10, ("baker",)), (4, 12, ("korobov", 1))]
 
 
 @pytest.mark.parametrize("fam,d,tr", GENZ_CASES)
@@ -144,6 +147,22 @@ def test_genz_sums_match_oracle(env, fam, d, tr):
     assert abs(res[0] - qbar) <= TOL * A.mean()
     assert abs(res[1] - sig) <= max(1e-9 * sig, 2e-12 * A.mean())
     assert cnt[0] == 0
+
+
+@pytest.mark.parametrize("fam", [1, 3, 4, 5, 6])
+def test_genz_outside_fixed_point_range(env, fam):
+    """Parameters outside the Genz ranges (a negative c_j, w_j > 1) take the FP64 form of
+    the integrand; results still match the oracle."""
+    q, torch, dev, tab = env
+    n, d, m = 4691, 4, 8
+    c = np.array([1.5, -0.75, 2.0, 0.5])
+    w = np.array([0.3, 1.25, 0.6, 0.1])
+    z = tab.z_for(n)[:d]
+    D = O.shifts(77 + fam, m, d)
+    for tr in (("korobov", 3), ("baker",)):
+        res, gre, _, cnt = _gpu_sums(env, q.Integrand.genz(fam, c, w), n, z, D, tr)
+        o = O.shift_sums(O.genz(fam, c, w), tr, n, z, D)
+        _compare(gre, None, o, n)
 
 
 def test_config1_product_peak_full_size(env):

@@ -69,34 +69,9 @@ inline TransformParams make_transform(const qmc_transform &t) {
         // binomial expansion of (1-t)^r1 integrated term by term (Eq. (korobov)).
         for (int k = 0; k <= r1; ++k) tp.A[k] = tp.C * ((k & 1) ? -1.0 : 1.0) * binom(r1, k) / (r0 + k + 1);
         for (int k = 0; k <= r0; ++k) tp.B[k] = tp.C * ((k & 1) ? -1.0 : 1.0) * binom(r0, k) / (r1 + k + 1);
-        if (r0 == r1 && r0 >= 1 && r0 <= kMaxKorobovInt) {
-            // integer coefficients A_k = C binom(r,k) / (r+1+k) (exact for r <= 4) and the
-            // largest F such that every Horner intermediate, bounded by
-            // M = max_k sum_{j >= k} |A_j| 2^-(j-k) on v <= 1/2, stays below 2^62 / (M + 1)
-            const int r = r0;
-            long long Ci = (2 * r + 1), Ai[kMaxKorobovInt + 1];
-            for (int i = 1; i <= r; ++i) Ci = Ci * (r + i) / i;       // (2r+1) binom(2r, r)
-            bool exact = true;
-            for (int k = 0; k <= r; ++k) {
-                long long b = 1;
-                for (int i = 1; i <= k; ++i) b = b * (r - k + i) / i;   // binom(r, k)
-                exact = exact && (Ci * b) % (r + 1 + k) == 0;
-                Ai[k] = ((k & 1) ? -1 : 1) * (Ci * b / (r + 1 + k));
-            }
-            double M = 0.0;
-            for (int k = 0; k <= r; ++k) {
-                double s = 0.0;
-                for (int j = r; j >= k; --j) s = s * 0.5 + std::fabs((double)Ai[j]);
-                M = std::max(M, s);
-            }
-            int F = 0;
-            while (std::ldexp(M + 1.0, F + 1) <= std::ldexp(1.0, 62)) ++F;
-            if (exact) {
-                tp.kind = kTKorobovInt;
-                tp.kfix_F = F;
-                for (int k = 0; k <= r; ++k) tp.kfix[k] = Ai[k] * (1ll << F);
-            }
-        }
+        // Korobov<r,r> with r <= 4 has integer polynomial coefficients and runs on the
+        // integer pipe (the coefficients are compile-time constants of the kernel)
+        if (r0 == r1 && r0 >= 1 && r0 <= kMaxKorobovInt) tp.kind = kTKorobovInt;
     } else if (t.kind == QMC_T_SIDI) {
         const int r = t.r0;
         tp.r1 = r;

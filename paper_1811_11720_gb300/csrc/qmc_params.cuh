@@ -23,8 +23,6 @@ constexpr int kMaxKorobovInt = 4;
 // (B: r0 and r1 exchanged).  The weight is C u^r0 (1-u)^r1, C = (r0+r1+1) binom(r0+r1,r0).
 struct TransformParams {
     int kind, r0, r1, deg;        // deg = max(r0, r1): Horner length (zero-padded)
-    int kfix_F, kfix_pad;         // kTKorobovInt: fractional bits of the Horner scheme
-    long long kfix[kMaxKorobovInt + 1];   // kTKorobovInt: A_k 2^kfix_F (exact integers)
     double A[kMaxKorobov + 1];
     double B[kMaxKorobov + 1];
     double C;                     // Korobov constant, or Sidi (pi/2^r) Gamma(r+1)/Gamma((r+1)/2)^2

@@ -61,7 +61,7 @@ struct WarpLattice {
 
 // One evaluation of g at the point whose coordinate j has lattice state (fhi(j), flo(j),
 // rem(j)); adds it to the two-level accumulator.
-template <int FAM, int TK, class P, class Hi, class Lo, class Rem>
+template <int FAM, int TK, int R, class P, class Hi, class Lo, class Rem>
 __device__ __forceinline__ void eval_point(const P &p, const FamilyShared &fsh, const double *s_fit,
                                            bool use_fit, const uint64_t *dsh, double cd, Hi fhi,
                                            Lo flo, Rem rem, double &g_re, double &g_im,
@@ -74,8 +74,8 @@ __device__ __forceinline__ void eval_point(const P &p, const FamilyShared &fsh, 
         if (!use_fit && fsh.fx.ok) {
             fa.init_fixed();
 #pragma unroll 1
-            for (int j = 0; j < p.d; ++j) fa.add_fixed(j, transform_fixed<TK>(fhi(j) + dsh[j], p.t, W), fsh);
-            const double wt = weight_finish<TK>(W, p.t, cd);
+            for (int j = 0; j < p.d; ++j) fa.add_fixed(j, transform_fixed<TK, R>(fhi(j) + dsh[j], W), fsh);
+            const double wt = weight_finish<TK, R>(W, p.t, cd);
             fa.finish_fixed(p.d, fsh, g_re, g_im, signfail);
             g_re *= wt;
             return;
@@ -86,7 +86,7 @@ __device__ __forceinline__ void eval_point(const P &p, const FamilyShared &fsh, 
     for (int j = 0; j < p.d; ++j) {
         Mapped mx;
         if constexpr (TK == kTKorobovInt) {
-            mx = korobov_int_x(fhi(j) + dsh[j], p.t, W);
+            mx = korobov_int_x<R>(fhi(j) + dsh[j], W);
         } else {
             const double u = fixed_to_double(fhi(j) + dsh[j], flo(j), rem(j), p.n);
             mx = apply_transform<TK>(u, p.t, W);
@@ -94,7 +94,7 @@ __device__ __forceinline__ void eval_point(const P &p, const FamilyShared &fsh, 
         if (use_fit) mx = Mapped{apply_fit(reflected(mx), s_fit + kFitStride * j, W.w), false};
         fa.add(j, mx, fsh);
     }
-    const double wt = weight_finish<TK>(W, p.t, cd);
+    const double wt = weight_finish<TK, R>(W, p.t, cd);
     fa.finish(p.d, fsh, g_re, g_im, signfail);
     g_re *= wt;
     if constexpr (FamilyAcc<FAM>::kComplex) g_im *= wt;
@@ -110,13 +110,13 @@ __device__ __forceinline__ void eval_point(const P &p, const FamilyShared &fsh, 
 // per point; every lane reads the d coordinates from there (broadcast loads).  That is one
 // lattice step per lane and point instead of d.  Otherwise each thread keeps all d
 // coordinates in local memory (L1) and steps them itself.
-template <int FAM, int TK, class P>
-__device__ __forceinline__ void stream_sums(const P &p, const FamilyShared &fsh, const double *s_fit,
-                                            bool use_fit, const uint64_t *dsh, double cd,
-                                            uint64_t i0, uint64_t cnt, WarpLattice *wl,
-                                            double &acc_re, double &acc_im,
-                                            unsigned long long &nonfinite,
-                                            unsigned long long &signfail) {
+template <int FAM, int TK, int R, class P>
+__device__ __forceinline__ void stream_sums_r(const P &p, const FamilyShared &fsh, const double *s_fit,
+                                              bool use_fit, const uint64_t *dsh, double cd,
+                                              uint64_t i0, uint64_t cnt, WarpLattice *wl,
+                                              double &acc_re, double &acc_im,
+                                              unsigned long long &nonfinite,
+                                              unsigned long long &signfail) {
     constexpr bool kCplx = FamilyAcc<FAM>::kComplex;
     const int d = p.d;
     const uint64_t n = p.n;
@@ -153,7 +153,7 @@ __device__ __forceinline__ void stream_sums(const P &p, const FamilyShared &fsh,
             }
             __syncwarp();
             double g_re, g_im = 0.0;
-            eval_point<FAM, TK>(
+            eval_point<FAM, TK, R>(
                 p, fsh, s_fit, use_fit, dsh, cd, [&](int j) { return wl->fhi[b][j]; },
                 [&](int j) { return wl->flo[b][j]; }, [&](int j) { return wl->rem[b][j]; }, g_re,
                 g_im, signfail);
@@ -167,7 +167,7 @@ __device__ __forceinline__ void stream_sums(const P &p, const FamilyShared &fsh,
 #pragma unroll 1
         for (uint64_t t = 0; t < cnt; ++t) {
             double g_re, g_im = 0.0;
-            eval_point<FAM, TK>(
+            eval_point<FAM, TK, R>(
                 p, fsh, s_fit, use_fit, dsh, cd, [&](int j) { return fhi[j]; },
                 [&](int j) { return flo[j]; }, [&](int j) { return rem[j]; }, g_re, g_im, signfail);
             accumulate(t, g_re, g_im);
@@ -177,6 +177,39 @@ __device__ __forceinline__ void stream_sums(const P &p, const FamilyShared &fsh,
     }
     acc_re += in_re;
     if constexpr (kCplx) acc_im += in_im;
+}
+
+// The integer Korobov is compiled once per order r (uniform branch per stream).
+template <int FAM, int TK, class P>
+__device__ __forceinline__ void stream_sums(const P &p, const FamilyShared &fsh, const double *s_fit,
+                                            bool use_fit, const uint64_t *dsh, double cd,
+                                            uint64_t i0, uint64_t cnt, WarpLattice *wl,
+                                            double &acc_re, double &acc_im,
+                                            unsigned long long &nonfinite,
+                                            unsigned long long &signfail) {
+    if constexpr (TK == kTKorobovInt) {
+        switch (p.t.r0) {
+        case 1:
+            stream_sums_r<FAM, TK, 1>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, acc_re, acc_im,
+                                      nonfinite, signfail);
+            return;
+        case 2:
+            stream_sums_r<FAM, TK, 2>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, acc_re, acc_im,
+                                      nonfinite, signfail);
+            return;
+        case 3:
+            stream_sums_r<FAM, TK, 3>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, acc_re, acc_im,
+                                      nonfinite, signfail);
+            return;
+        default:
+            stream_sums_r<FAM, TK, 4>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, acc_re, acc_im,
+                                      nonfinite, signfail);
+            return;
+        }
+    } else {
+        stream_sums_r<FAM, TK, 0>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, acc_re, acc_im,
+                                  nonfinite, signfail);
+    }
 }
 
 // Per-shift tile partial: fixed-order compensated sum over the block's spb streams of

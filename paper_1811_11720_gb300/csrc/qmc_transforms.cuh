@@ -85,11 +85,12 @@ __device__ __forceinline__ Mapped apply_transform(double u, const TransformParam
     }
 }
 
-// The integer-pipe Korobov<r,r> (kTKorobovInt) takes the lattice state's top word
+// The integer-pipe Korobov<R,R> (kTKorobovInt) takes the lattice state's top word
 // X = x 2^64 instead of the rounded u: v = min(x, 1 - x) in 0.64 fixed point.
-__device__ __forceinline__ Mapped korobov_int_x(uint64_t X, const TransformParams &t, Weight &W) {
+template <int R>
+__device__ __forceinline__ Mapped korobov_int_x(uint64_t X, Weight &W) {
     const bool lo = !(X >> 63);
-    return {korobov_int(lo ? X : ~X, t, W.wp), !lo};
+    return {fixed_to_double64(korobov_phi_fixed<R>(lo ? X : ~X, W.wp)), !lo};
 }
 
 // Transforms that are exact or fixed-point on the integer pipe can hand the integrand the
@@ -99,8 +100,8 @@ __device__ __forceinline__ Mapped korobov_int_x(uint64_t X, const TransformParam
 template <int TK>
 constexpr bool kFixedTransform = TK == QMC_T_NONE || TK == QMC_T_BAKER || TK == kTKorobovInt;
 
-template <int TK>
-__device__ __forceinline__ uint64_t transform_fixed(uint64_t X, const TransformParams &t, Weight &W) {
+template <int TK, int R>
+__device__ __forceinline__ uint64_t transform_fixed(uint64_t X, Weight &W) {
     if constexpr (TK == QMC_T_NONE) {
         return X;
     } else if constexpr (TK == QMC_T_BAKER) {
@@ -108,20 +109,20 @@ __device__ __forceinline__ uint64_t transform_fixed(uint64_t X, const TransformP
     } else {
         static_assert(TK == kTKorobovInt, "no fixed-point form");
         const bool lo = !(X >> 63);
-        const uint64_t F = fx_to_fixed(korobov_int_phi(lo ? X : ~X, t, W.wp));
+        const uint64_t F = korobov_phi_fixed<R>(lo ? X : ~X, W.wp);
         return lo ? F : ~F;
     }
 }
 
 // cd = C^d for Korobov (folded once per launch).
-template <int TK>
+template <int TK, int R = 0>
 __device__ __forceinline__ double weight_finish(const Weight &W, const TransformParams &t,
                                                 double cd) {
     if constexpr (TK == QMC_T_KOROBOV) {
         if (t.r0 == t.r1) return cd * ipow_u(W.wu, t.r0) * W.w;
         return cd * ipow_u(W.wu, t.r0) * ipow_u(W.w1, t.r1) * W.w;
     } else if constexpr (TK == kTKorobovInt) {
-        return korobov_int_weight(W.wp, t.r0, fx_of_double(cd)) * W.w;
+        return korobov_weight_fixed<R>(W.wp, fx_of_double(cd)) * W.w;
     } else {
         return W.w;
     }

@@ -78,6 +78,24 @@ def fp64_flops_per_eval(family: int, transform, d: int) -> int:
     return tr + fam + 2
 
 
+def feynman_flops_per_eval(fl) -> int:
+    """Algorithmic FP64 work of one evaluation of the complex deformed integrand U^a F^-b
+    det J (config 3), counted as in the design notes' table (add/mul = 1, fma = 2, each
+    library call = 1): value, gradient and Hessian of F (one fused multiply-add per term and
+    derivative, nf (1 + d + d(d+1)/2) of them), U and F at the complex point (a complex
+    multiply-add per factor: 8 flops), the deformation and the Jacobian entries (3d + 2d^2),
+    complex LU of the d x d Jacobian (8 d^3 / 3), two complex powers (hypot, atan2, log, exp,
+    sincos: 5 calls + 4 flops each), two complex products and the weighted accumulation."""
+    d = fl.d
+    nf, nu = fl.F.nterms, fl.U.nterms
+    factors = int(fl.U.exps.sum() + fl.F.exps.sum())
+    derivs = 2 * nf * (1 + d + d * (d + 1) // 2)
+    complex_vals = 8 * factors + 2 * 2 * (nu + nf)
+    deform = 3 * d + 2 * d * d
+    lu = (8 * d ** 3) // 3
+    return derivs + complex_vals + deform + lu + 2 * 9 + 12 + 4
+
+
 def parse_transform(tok: str):
     if tok == "baker":
         return ("baker",)
@@ -86,9 +104,18 @@ def parse_transform(tok: str):
     raise ValueError(tok)
 
 
-def workload_items(rank: int = 0, only: str | None = None):
-    """The 45 (family, d, transform) integrals, or the single one named by ``only``
-    ("FAMILY:D:TRANSFORM", e.g. "4:10:korobov3") for profiling a small case."""
+FEYNMAN_FAMILY = 20
+FEYNMAN_INTEGRALS = 4
+
+
+def workload_items(rank: int = 0, only: str | None = None, workload: str = "genz"):
+    """The 45 (family, d, transform, c, w) Genz integrals, or the single one named by
+    ``only`` ("FAMILY:D:TRANSFORM", e.g. "4:10:korobov3") for profiling a small case.
+    workload "feynman" (config 3): four d = 5 complex deformed integrands
+    (workloads.feynman_regular) with Korobov-3, as (20, 5, transform, FeynmanLike, None)."""
+    if workload == "feynman":
+        return [(FEYNMAN_FAMILY, 5, ("korobov", 3), W.feynman_regular(1000 + 17 * rank + k), None)
+                for k in range(FEYNMAN_INTEGRALS)]
     items = []
     for fam in FAMILIES:
         for d in DIMS:
@@ -172,19 +199,20 @@ def run_gpu(args, rank: int, world: int):
     table = q.GenvecTable.load()
     n = args.n
     zfull = table.z_for(n)
-    items = workload_items(rank, args.only)
+    items = workload_items(rank, args.only, args.workload)
     stream = torch.cuda.current_stream(dev)
+    cplx = args.workload == "feynman"
 
     # resident inputs: coefficients, shifts, workspace, outputs
     prepared = []
     max_ws = 0
     for idx, (fam, d, tr, c, w) in enumerate(items):
-        f = q.Integrand.genz(fam, c, w)
+        f = q.Integrand.polynomial(c) if fam == FEYNMAN_FAMILY else q.Integrand.genz(fam, c, w)
         D = q.make_shifts(args.seed + 7919 * rank + idx, M_SHIFTS, d)
         Dd = torch.from_numpy(D.astype(np.int64)).to(dev)
         r = q.rule(n, zfull[:d], Dd, tr)
         fd = f.device_struct(dev)
-        max_ws = max(max_ws, q.sums_workspace_bytes(r, False, 0, n))
+        max_ws = max(max_ws, q.sums_workspace_bytes(r, cplx, 0, n))
         prepared.append((fam, d, tr, f, fd, r, Dd, D))
     ws = torch.empty(max_ws, dtype=torch.uint8, device=dev)
     sums = torch.empty(len(items), 4 * M_SHIFTS, dtype=torch.float64, device=dev)
@@ -192,7 +220,8 @@ def run_gpu(args, rank: int, world: int):
     cnt = torch.zeros(2, dtype=torch.int64, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
     evals_per_step = len(items) * n * M_SHIFTS
-    flops_per_step = sum(fp64_flops_per_eval(fam, tr, d) for fam, d, tr, *_ in items) * n * M_SHIFTS
+    flops_per_step = sum(feynman_flops_per_eval(c) if fam == FEYNMAN_FAMILY else
+                         fp64_flops_per_eval(fam, tr, d) for fam, d, tr, c, _ in items) * n * M_SHIFTS
 
     ev_k = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
             for _ in items]
@@ -205,7 +234,7 @@ def run_gpu(args, rank: int, world: int):
             q.sums(fd, r, 0, n, ws, sums[i], cnt, stream)
             if time_kernels:
                 ev_k[i][1].record(stream)
-            q.finalize(sums[i], M_SHIFTS, n, False, res[i], None, stream)
+            q.finalize(sums[i], M_SHIFTS, n, cplx, res[i], None, stream)
         if time_kernels:
             torch.cuda.synchronize(dev)
             kt = sum(a.elapsed_time(b) for a, b in ev_k)
@@ -255,7 +284,8 @@ def run_gpu(args, rank: int, world: int):
         for (fam, d, tr, f, fd, r, Dd, D), (_, _, _, c, w) in zip(prepared, items):
             out = q.integrate(f, table, n, M_SHIFTS, tr, seed=args.seed + 7919 * rank, stream=stream)
             if it == 0:
-                h2d += c.nbytes + w.nbytes + M_SHIFTS * d * 8
+                h2d += M_SHIFTS * d * 8 + (c.nbytes + w.nbytes if fam != FEYNMAN_FAMILY else
+                                           sum(a.nbytes for a in (c.U.coef, c.U.exps, c.F.coef, c.F.exps)))
         torch.cuda.synchronize(dev)
         if it > 0:                         # first pass warms the library's arena
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
@@ -270,7 +300,7 @@ def run_gpu(args, rank: int, world: int):
         "total_ms": total_ms, "step_ms": step_ms, "evals_per_step": evals_per_step,
         "flops_per_step": flops_per_step, "kernel_ms_per_launch": k_per_launch_ms,
         "clocks": clocks, "e2e_total_ms": e2e_total, "e2e_steps": args.e2e_steps,
-        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(items) * (4 * 8 + 2 * 8),
+        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(items) * ((8 if cplx else 4) * 8 + 2 * 8),
         "nonfinite": nonfinite, "results": from_host, "items": items,
         "launches_per_step": len(items) * 3,
     }
@@ -387,12 +417,24 @@ def run_batch_workload(args):
     print(json.dumps(line))
 
 
+SERVE_EPSABS = 1e-7   # the library's default absolute goal (App. A.1)
+
+
+def goal_met(res, epsrel: float, epsabs: float = SERVE_EPSABS) -> bool:
+    """The adaptive mode's goal per component (errormode all):
+    |error| <= max(epsabs, epsrel |integral|) for the real and the imaginary part."""
+    I, E = res["integral"], res["error"]
+    return (abs(E.real) <= max(epsabs, epsrel * abs(I.real)) and
+            abs(E.imag) <= max(epsabs, epsrel * abs(I.imag)))
+
+
 def run_serve_workload(args):
     """Serving: Poisson arrivals of config-3-like integrals (complex, d = 5, contour
-    deformation, Korobov-3, m = 32), each with a relative error target log-uniform in
-    [1e-8, 1e-3] and an evaluation budget; continuous batching (qmc_server) against the
-    same arrival stream served one integral at a time (qmc_integrate, adaptive).  Reports
-    p50/p99 latency (arrival to completion) and integrals/s for both."""
+    deformation with lam = 1, Korobov-3, m = 32; half with F > 0 on the cube, half with F
+    changing sign inside), each with a relative error target log-uniform in [1e-8, 1e-3],
+    the library's default absolute target 1e-7, and an evaluation budget; continuous batching (qmc_server) against the same arrival
+    stream served one integral at a time (qmc_integrate, adaptive).  Reports p50/p99
+    latency (arrival to completion), integrals/s and the number of goals met for both."""
     import torch
 
     import paper_1811_11720_gb300 as q
@@ -404,12 +446,15 @@ def run_serve_workload(args):
     N = args.requests
     reqs = []
     for i in range(N):
-        f = q.Integrand.polynomial(W.feynman_regular(args.seed + i))
+        # alternately Euclidean-like (F > 0 on the cube, beta = 0.6) and with F changing
+        # sign inside (beta = 0.95); lam = 1 keeps F(z) away from zero
+        beta = 0.6 if i % 2 == 0 else 0.95
+        f = q.Integrand.polynomial(W.feynman_regular(args.seed + i, beta=beta, lam=1.0))
         eps = float(10 ** rng.uniform(-8, -3))
         reqs.append((f, eps))
     out = {"metric": "served integrals/s", "unit": "integrals/s", "higher_is_better": True,
            "n_gpus": 1, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "feynman_d5_korobov3_m32_eps1e-8..1e-3_poisson",
+           "config": {"workload": "feynman_regular_d5_beta0.6|0.95_lam1_korobov3_m32_eps1e-8..1e-3_poisson",
                       "requests": N, "maxeval": args.serve_maxeval}, "rates": []}
 
     def arrivals(rate):
@@ -429,7 +474,7 @@ def run_serve_workload(args):
             now = time.perf_counter() - t0
             while nxt < N and t_arr[nxt] <= now:
                 f, eps = reqs[nxt]
-                ids[nxt] = srv.submit(f, epsrel=eps, epsabs=0.0, minn=1021,
+                ids[nxt] = srv.submit(f, epsrel=eps, epsabs=SERVE_EPSABS, minn=1021,
                                       maxeval=int(args.serve_maxeval), seed=nxt)
                 open_ids[ids[nxt]] = nxt
                 nxt += 1
@@ -443,9 +488,8 @@ def run_serve_workload(args):
                 time.sleep(max(0.0, t_arr[nxt] - (time.perf_counter() - t0)))
         span_b = max(done_t) - t_arr[0]
         lat_b = np.array(done_t) - t_arr
-        met_b = sum(srv.status(ids[i])["err"] <= reqs[i][1] * abs(srv.status(ids[i])["integral"])
-                    for i in range(N))
         res_b = [srv.status(ids[i]) for i in range(N)]
+        met_b = sum(goal_met(res_b[i], reqs[i][1]) for i in range(N))
         srv.close()
         # one integral at a time, FIFO, same arrivals
         done_s = [None] * N
@@ -457,18 +501,19 @@ def run_serve_workload(args):
                 time.sleep(t_arr[i] - now)
             f, eps = reqs[i]
             r = q.integrate(f, table, 1021, M_SHIFTS, ("korobov", 3), seed=i,
-                            opts=q.options(epsrel=eps, epsabs=0.0, maxeval=int(args.serve_maxeval)))
+                            opts=q.options(epsrel=eps, epsabs=SERVE_EPSABS, maxeval=int(args.serve_maxeval)))
             done_s[i] = time.perf_counter() - t0
             res_s.append(r)
         span_s = max(done_s) - t_arr[0]
         lat_s = np.array(done_s) - t_arr
         same = all(rb["integral"] == rs["integral"] for rb, rs in zip(res_b, res_s))
+        met_s = sum(goal_met(res_s[i], reqs[i][1]) for i in range(N))
         out["rates"].append({
             "rate_per_s": rate,
             "batched": {"integrals_per_s": N / span_b, "p50_s": float(np.percentile(lat_b, 50)),
                         "p99_s": float(np.percentile(lat_b, 99)), "goal_met": int(met_b)},
             "one_at_a_time": {"integrals_per_s": N / span_s, "p50_s": float(np.percentile(lat_s, 50)),
-                              "p99_s": float(np.percentile(lat_s, 99))},
+                              "p99_s": float(np.percentile(lat_s, 99)), "goal_met": int(met_s)},
             "same_results": bool(same)})
     best = out["rates"][-1]
     out["value"] = best["batched"]["integrals_per_s"]
@@ -486,10 +531,13 @@ def cpu_baseline(budget_s: float, items, nthreads: int | None = None):
     z = tab[N_LATTICE]
     nthreads = nthreads or os.cpu_count()
     # calibrate the prefix length on the first item, then give every item the same share
+    def integrand(fam, c, w):
+        return O.feynman_complex(c) if fam == FEYNMAN_FAMILY else O.genz(fam, c, w)
+
     fam, d, tr, c, w = items[0]
     D = O.shifts(1, M_SHIFTS, d)
     t0 = time.perf_counter()
-    O.shift_sums(O.genz(fam, c, w), tr, N_LATTICE, z, D, i0=0, i1=2048, nthreads=nthreads)
+    O.shift_sums(integrand(fam, c, w), tr, N_LATTICE, z, D, i0=0, i1=2048, nthreads=nthreads)
     dt = time.perf_counter() - t0
     rate = 2048 * M_SHIFTS / max(dt, 1e-6)
     per_item = max(1024, int(budget_s / len(items) * rate / M_SHIFTS))
@@ -498,7 +546,7 @@ def cpu_baseline(budget_s: float, items, nthreads: int | None = None):
     t0 = time.perf_counter()
     for (fam, d, tr, c, w) in items:
         D = O.shifts(1, M_SHIFTS, d)
-        O.shift_sums(O.genz(fam, c, w), tr, N_LATTICE, z, D, i0=0, i1=per_item, nthreads=nthreads)
+        O.shift_sums(integrand(fam, c, w), tr, N_LATTICE, z, D, i0=0, i1=per_item, nthreads=nthreads)
         evals += per_item * M_SHIFTS
     el = time.perf_counter() - t0
     return {"value": evals / el, "unit": "evals/s", "cores": nthreads, "kind": "oracle",
@@ -518,7 +566,7 @@ def main():
     ap.add_argument("--no-kernel-events", dest="kernel_events", action="store_false")
     ap.add_argument("--only", default=None, help="FAMILY:D:TRANSFORM, e.g. 4:10:korobov3")
     ap.add_argument("--n", type=int, default=N_LATTICE, help="lattice size (a table size)")
-    ap.add_argument("--workload", default="genz", choices=["genz", "batch", "serve"])
+    ap.add_argument("--workload", default="genz", choices=["genz", "feynman", "batch", "serve"])
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--rates", type=float, nargs="*", default=[2.0, 8.0, 32.0])
     ap.add_argument("--serve-maxeval", type=float, default=3.2e7)
@@ -538,9 +586,11 @@ def main():
     base = {"metric": "FP64 integrand evals/sec", "unit": "evals/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": (f"genz_osc_corner_gauss_d6_8_10_baker_korobov1-4_n{args.n}_m32"
+            "config": {"workload": (f"feynman_regular_d5_complex_korobov3_n{args.n}_m32"
+                                    if args.workload == "feynman" else
+                                    f"genz_osc_corner_gauss_d6_8_10_baker_korobov1-4_n{args.n}_m32"
                                     if not args.only else f"genz_{args.only}_n{args.n}_m32"),
-                       "integrals_per_step": len(workload_items(0, args.only)),
+                       "integrals_per_step": len(workload_items(0, args.only, args.workload)),
                        "n": args.n, "m": M_SHIFTS, "l2": "flushed between steps",
                        "parallelism": f"replicas x{args.gpus} (independent integrals per rank)"}}
 
@@ -551,7 +601,7 @@ def main():
             if rank != 0:
                 dist.destroy_process_group()
                 return
-        items = workload_items(0)
+        items = workload_items(0, args.only, args.workload)
         per_step = []
         samples = []
         for _ in range(args.warmup):
@@ -611,7 +661,7 @@ def main():
             "nonfinite": r["nonfinite"],
         })
         if world == 1 and args.cpu_budget > 0:
-            line["cpu_baseline"] = cpu_baseline(args.cpu_budget, workload_items(0, args.only))
+            line["cpu_baseline"] = cpu_baseline(args.cpu_budget, workload_items(0, args.only, args.workload))
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -44,7 +44,19 @@ struct PolyShared {
     uint16_t ukey[kMaxTerms], fkey[kMaxTerms];     // dense keys as a cubic
     uint16_t ukey2[kMaxTerms], fkey2[kMaxTerms];   // dense keys as a quadratic (0xFFFF: degree 3)
     int maxdeg_u, maxdeg_f;
+    int feyn_dense;   // complex family: symmetric-tensor form (see stage_feynman_tensors)
 };
+
+// Symmetric-tensor form of the complex family (deg U <= 2, deg F <= 3, d <= kFeynDenseMaxDim):
+//   U = u0 + sum_i u1_i x_i + sum_ij U2_ij x_i x_j,
+//   F = f0 + sum_i f1_i x_i + sum_ij F2_ij x_i x_j + sum_ijk F3_ijk x_i x_j x_k
+// with U2, F2, F3 fully symmetric (a monomial's coefficient shared equally by the
+// permutations of its factors).  Layout in buf: U at [0]: u0, u1[d], U2[d][d];
+// F at [2 kMaxTerms]: f0, f1[d], F2[d][d], F3[pair(i <= j)][k] (row-major upper triangle).
+constexpr int kFeynDenseMaxDim = 11;   // 1 + d + d^2 + d^2 (d+1)/2 <= 2 kMaxTerms
+__device__ __forceinline__ int feyn_pair(int i, int j, int d) {   // i <= j
+    return i * d - i * (i - 1) / 2 + (j - i);
+}
 
 __device__ __forceinline__ double ps_ucoef(const PolyShared &ps, int q) { return ps.buf.v[q]; }
 __device__ __forceinline__ double ps_fcoef(const PolyShared &ps, int q) { return ps.buf.v[2 * kMaxTerms + q]; }
@@ -95,8 +107,66 @@ __device__ __forceinline__ int monomial_key(const int32_t *e, int d, int D, int 
     return dense_index(f, D, d + 1);
 }
 
-// allow_dense: the real sector family evaluates through the dense form when cheaper; the
-// complex deformed family keeps the sparse list (its derivatives use the factor lists).
+// Adds coefficient c of monomial e (degree <= 3) to the symmetric tensors at base
+// (constant, linear, square matrix, then for deg 3 the F3[pair][k] block when t3 != null).
+__device__ __forceinline__ void feyn_add_term(double *base, double *t3, const int32_t *e, int d,
+                                              double c) {
+    int f[3];
+    int n = 0;
+    for (int k = 0; k < d; ++k)
+        for (int q = 0; q < e[k] && n < 3; ++q) f[n++] = k;
+    double *lin = base + 1, *sq = base + 1 + d;
+    if (n == 0) {
+        base[0] += c;
+    } else if (n == 1) {
+        lin[f[0]] += c;
+    } else if (n == 2) {
+        if (f[0] == f[1]) {
+            sq[f[0] * d + f[0]] += c;
+        } else {
+            sq[f[0] * d + f[1]] += 0.5 * c;
+            sq[f[1] * d + f[0]] += 0.5 * c;
+        }
+    } else {
+        const int a = f[0], b = f[1], e3 = f[2];   // a <= b <= e3
+        if (a == b && b == e3) {
+            t3[feyn_pair(a, a, d) * d + a] += c;
+        } else if (a == b) {          // a a e3: (aa, e3), (a e3, a)
+            t3[feyn_pair(a, a, d) * d + e3] += c / 3.0;
+            t3[feyn_pair(a, e3, d) * d + a] += c / 3.0;
+        } else if (b == e3) {         // a b b: (ab, b), (bb, a)
+            t3[feyn_pair(a, b, d) * d + b] += c / 3.0;
+            t3[feyn_pair(b, b, d) * d + a] += c / 3.0;
+        } else {                      // distinct: (ab, e3), (a e3, b), (b e3, a)
+            t3[feyn_pair(a, b, d) * d + e3] += c / 6.0;
+            t3[feyn_pair(a, e3, d) * d + b] += c / 6.0;
+            t3[feyn_pair(b, e3, d) * d + a] += c / 6.0;
+        }
+    }
+}
+
+// FP64 operations per evaluation of the two forms of the complex family (derivatives,
+// values at the complex point; the Jacobian and powers are common).
+__device__ __forceinline__ bool feyn_tensor_cheaper(const PolyShared &ps, const int32_t *uexp,
+                                                    const int32_t *fexp, int d) {
+    if (d > kFeynDenseMaxDim || ps.maxdeg_u > 2 || ps.maxdeg_f > 3) return false;
+    int sparse = 0;
+    for (int q = 0; q < ps.nf; ++q) {
+        int deg = 0;
+        for (int k = 0; k < d; ++k) deg += fexp[(size_t)q * d + k];
+        sparse += 2 * deg * deg + 8 * deg + 2;
+    }
+    for (int q = 0; q < ps.nu; ++q) {
+        int deg = 0;
+        for (int k = 0; k < d; ++k) deg += uexp[(size_t)q * d + k];
+        sparse += 8 * deg + 2;
+    }
+    const int dense = d * d * (d + 1) + 7 * d * d + 10 * d;
+    return dense < sparse;
+}
+
+// allow_dense: the real sector family evaluates through the dense Horner form when
+// cheaper; the complex deformed family uses the symmetric-tensor form when cheaper.
 template <class P>
 __device__ __forceinline__ void stage_poly(const P &p, PolyShared &ps, bool allow_dense) {
     const int tid = threadIdx.x;
@@ -139,10 +209,28 @@ __device__ __forceinline__ void stage_poly(const P &p, PolyShared &ps, bool allo
     const int sparse_u = p.nu * (ps.maxdeg_u + 1), sparse_f = p.nf * (ps.maxdeg_f + 1);
     const int use_u = (du && (du == 2 ? cost2 : cost3) < sparse_u) ? du : 0;
     const int use_f = (df && (df == 2 ? cost2 : cost3) < sparse_f) ? df : 0;
+    const bool tensors = !allow_dense && feyn_tensor_cheaper(ps, p.uexp, p.fexp, d);
     __syncthreads();   // every thread has read maxdeg before the buffers are rewritten
     if (tid == 0) {
         ps.dense_u = use_u;
         ps.dense_f = use_f;
+        ps.feyn_dense = tensors;
+    }
+    if (tensors) {
+        // one thread, input order: duplicates and symmetric slots summed deterministically
+        const int nU = 1 + d + d * d;
+        const int nF = nU + d * d * (d + 1) / 2;
+        for (int e = tid; e < nU; e += blockDim.x) ps.buf.v[e] = 0.0;
+        for (int e = tid; e < nF; e += blockDim.x) ps.buf.v[2 * kMaxTerms + e] = 0.0;
+        __syncthreads();
+        if (tid == 0) {
+            for (int q = 0; q < p.nu; ++q)
+                feyn_add_term(ps.buf.v, nullptr, p.uexp + (size_t)q * d, d, p.ucoef[q]);
+            double *fb = ps.buf.v + 2 * kMaxTerms;
+            for (int q = 0; q < p.nf; ++q)
+                feyn_add_term(fb, fb + nU, p.fexp + (size_t)q * d, d, p.fcoef[q]);
+        }
+        return;
     }
     if (use_u) {
         // re-key as a quadratic when the dense form is quadratic
@@ -254,21 +342,165 @@ __device__ __forceinline__ cplx crecip(cplx a) {
     return {a.re * s, -a.im * s};
 }
 
-// principal a^p for real p: exp(p Log a)
-__device__ __forceinline__ cplx cpow_real(cplx a, double p) {
-    if (p == 1.0) return a;
-    double r = hypot(a.re, a.im);
-    double th = atan2(a.im, a.re);
-    double lr = log(r);
-    double mag = exp(p * lr);
-    double s, c;
-    sincos(p * th, &s, &c);
-    return {mag * c, mag * s};
+
+// log a = (log |a|, arg a), principal branch.
+__device__ __forceinline__ cplx clog_principal(cplx a) {
+    const double n2 = fma(a.re, a.re, a.im * a.im);
+    // |a|^2 stays normal for the magnitudes met here; otherwise take log(hypot)
+    const double lr = (n2 > 1e-300 && n2 < 1e300) ? 0.5 * log(n2) : log(hypot(a.re, a.im));
+    return {lr, atan2(a.im, a.re)};
+}
+
+// det J = det(I - i lam (D H + E)), D = diag(x (1 - x)), E = diag((1 - 2x) g), by
+// elimination without pivoting (see the header comment); H is d x d in local memory.
+__device__ __forceinline__ cplx feynman_jacobian_det(const double *x, const double *xo,
+                                                     const double *g, const double *H, int d,
+                                                     double lam) {
+    cplx A[kMaxDim * kMaxDim];
+#pragma unroll 1
+    for (int k = 0; k < d; ++k)
+#pragma unroll 1
+        for (int l = 0; l < d; ++l) {
+            double mkl = xo[k] * H[k * d + l];
+            if (k == l) mkl = fma(1.0 - 2.0 * x[k], g[k], mkl);
+            A[k * d + l] = {(k == l) ? 1.0 : 0.0, -lam * mkl};
+        }
+    cplx det = {1.0, 0.0};
+#pragma unroll 1
+    for (int c = 0; c < d; ++c) {
+        cplx piv = A[c * d + c];
+        det = cmul(det, piv);
+        if (c + 1 == d) break;
+        cplx inv = crecip(piv);
+#pragma unroll 1
+        for (int r = c + 1; r < d; ++r) {
+            cplx l = cmul(A[r * d + c], inv);
+#pragma unroll 1
+            for (int q = c + 1; q < d; ++q) {
+                cplx a = A[c * d + q];
+                cplx &t = A[r * d + q];
+                t.re -= fma(l.re, a.re, -l.im * a.im);
+                t.im -= fma(l.re, a.im, l.im * a.re);
+            }
+        }
+    }
+    return det;
+}
+
+// U^a F^-b det for principal branches: exp(a Log U - b Log F) det (a = 1: U exp(-b Log F)).
+__device__ __forceinline__ void feynman_combine(cplx U, cplx F, cplx det, double pa, double pb,
+                                                double &re, double &im) {
+    const cplx lf = clog_principal(F);
+    double er = -pb * lf.re, ei = -pb * lf.im;
+    if (pa != 1.0) {
+        const cplx lu = clog_principal(U);
+        er = fma(pa, lu.re, er);
+        ei = fma(pa, lu.im, ei);
+    }
+    const double mag = exp(er);
+    double sn, cs;
+    sincos(ei, &sn, &cs);
+    cplx v = {mag * cs, mag * sn};
+    if (pa == 1.0) v = cmul(U, v);
+    v = cmul(v, det);
+    re = v.re;
+    im = v.im;
+}
+
+// Symmetric-tensor form (deg U <= 2, deg F <= 3).  At the real point x:
+//   H_ij = 2 F2_ij + 6 sum_k F3_ijk x_k,  g_i = f1_i + (F2 x)_i + (H x)_i / 2,
+//   F(x) = f0 + sum_i x_i (f1_i + (H x)_i / 6 + 2 (F2 x)_i / 3),
+// and at z = x + i y (y = -lam x (1 - x) g) the cubic's Taylor series is exact:
+//   F(z) = F(x) - y.H y / 2 + i (g.y - sum_ijk F3_ijk y_i y_j y_k),
+//   U(z) = U(x) - y.U2 y + i grad U.y,  grad U = u1 + 2 U2 x.
+static __device__ __noinline__ void feynman_value_dense(const double *xin, int d,
+                                                        const PolyShared &ps, double &re,
+                                                        double &im,
+                                                        unsigned long long &signfail) {
+    const double *ub = ps.buf.v;
+    const double *u1 = ub + 1, *U2 = ub + 1 + d;
+    const double *fb = ps.buf.v + 2 * kMaxTerms;
+    const double *f1 = fb + 1, *F2 = fb + 1 + d, *F3 = fb + 1 + d + d * d;
+    double x[kMaxDim], g[kMaxDim], y[kMaxDim], xo[kMaxDim];
+    double H[kMaxDim * kMaxDim];
+#pragma unroll 1
+    for (int k = 0; k < d; ++k) x[k] = xin[k];
+    // Hessian of F (symmetric)
+#pragma unroll 1
+    for (int i = 0; i < d; ++i)
+#pragma unroll 1
+        for (int j = i; j < d; ++j) {
+            const double *t = F3 + feyn_pair(i, j, d) * d;
+            double s = 0.0;
+#pragma unroll 1
+            for (int k = 0; k < d; ++k) s = fma(t[k], x[k], s);
+            const double h = fma(6.0, s, 2.0 * F2[i * d + j]);
+            H[i * d + j] = h;
+            H[j * d + i] = h;
+        }
+    // gradient, F(x), U(x), grad U
+    double Fx = 0.0, Ux = 0.0;
+    double gU[kMaxDim];
+#pragma unroll 1
+    for (int i = 0; i < d; ++i) {
+        double hx = 0.0, qx = 0.0, px = 0.0;
+#pragma unroll 1
+        for (int j = 0; j < d; ++j) {
+            hx = fma(H[i * d + j], x[j], hx);
+            qx = fma(F2[i * d + j], x[j], qx);
+            px = fma(U2[i * d + j], x[j], px);
+        }
+        g[i] = fma(0.5, hx, f1[i] + qx);
+        Fx = fma(x[i], fma(hx, 1.0 / 6.0, fma(qx, 2.0 / 3.0, f1[i])), Fx);
+        gU[i] = fma(2.0, px, u1[i]);
+        Ux = fma(x[i], u1[i] + px, Ux);
+    }
+    Fx += fb[0];
+    Ux += ub[0];
+    // deformation
+    const double lam = ps.lam;
+#pragma unroll 1
+    for (int k = 0; k < d; ++k) {
+        xo[k] = x[k] * (1.0 - x[k]);
+        y[k] = -lam * xo[k] * g[k];
+    }
+    // F(z), U(z)
+    double yHy = 0.0, gy = 0.0, yU2y = 0.0, gUy = 0.0, t3 = 0.0;
+#pragma unroll 1
+    for (int i = 0; i < d; ++i) {
+        double hy = 0.0, uy = 0.0;
+#pragma unroll 1
+        for (int j = 0; j < d; ++j) {
+            hy = fma(H[i * d + j], y[j], hy);
+            uy = fma(U2[i * d + j], y[j], uy);
+        }
+        yHy = fma(y[i], hy, yHy);
+        yU2y = fma(y[i], uy, yU2y);
+        gy = fma(g[i], y[i], gy);
+        gUy = fma(gU[i], y[i], gUy);
+#pragma unroll 1
+        for (int j = i; j < d; ++j) {
+            const double *t = F3 + feyn_pair(i, j, d) * d;
+            double s = 0.0;
+#pragma unroll 1
+            for (int k = 0; k < d; ++k) s = fma(t[k], y[k], s);
+            t3 = fma((i == j ? 1.0 : 2.0) * y[i] * y[j], s, t3);
+        }
+    }
+    const cplx Fz = {fma(-0.5, yHy, Fx), gy - t3};
+    const cplx Uz = {Ux - yU2y, gUy};
+    if (Fz.im > 0.0) ++signfail;
+    const cplx det = feynman_jacobian_det(x, xo, g, H, d, lam);
+    feynman_combine(Uz, Fz, det, ps.pa, ps.pb, re, im);
 }
 
 static __device__ __noinline__ void feynman_value(const double *xin, int d, const PolyShared &ps,
                                            double &re, double &im,
                                            unsigned long long &signfail) {
+    if (ps.feyn_dense) {
+        feynman_value_dense(xin, d, ps, re, im, signfail);
+        return;
+    }
     double x[kMaxDim];
     double grad[kMaxDim];
     double H[kMaxDim * kMaxDim];
@@ -337,41 +569,9 @@ static __device__ __noinline__ void feynman_value(const double *xin, int d, cons
         F.im = fma(ps_fcoef(ps, q), t.im, F.im);
     }
     if (F.im > 0.0) ++signfail;
-    // J_kl = delta_kl - i lam [delta_kl (1 - 2 x_k) dF_k + x_k (1 - x_k) d2F_kl]; Gaussian
-    // elimination without pivoting, det = product of the pivots.
-    cplx A[kMaxDim * kMaxDim];
-#pragma unroll 1
-    for (int k = 0; k < d; ++k)
-#pragma unroll 1
-        for (int l = 0; l < d; ++l) {
-            double mkl = xo[k] * H[k * d + l];
-            if (k == l) mkl = fma(1.0 - 2.0 * x[k], grad[k], mkl);
-            A[k * d + l] = {(k == l) ? 1.0 : 0.0, -lam * mkl};
-        }
-    cplx det = {1.0, 0.0};
-#pragma unroll 1
-    for (int c = 0; c < d; ++c) {
-        cplx piv = A[c * d + c];
-        det = cmul(det, piv);
-        if (c + 1 == d) break;
-        cplx inv = crecip(piv);
-#pragma unroll 1
-        for (int r = c + 1; r < d; ++r) {
-            cplx l = cmul(A[r * d + c], inv);
-#pragma unroll 1
-            for (int q = c + 1; q < d; ++q) {
-                cplx a = A[c * d + q];
-                cplx &t = A[r * d + q];
-                t.re -= fma(l.re, a.re, -l.im * a.im);
-                t.im -= fma(l.re, a.im, l.im * a.re);
-            }
-        }
-    }
-    cplx Ua = cpow_real(U, ps.pa);
-    cplx Fb = cpow_real(F, -ps.pb);
-    cplx v = cmul(cmul(Ua, Fb), det);
-    re = v.re;
-    im = v.im;
+    // J_kl = delta_kl - i lam [delta_kl (1 - 2 x_k) dF_k + x_k (1 - x_k) d2F_kl]
+    const cplx det = feynman_jacobian_det(x, xo, grad, H, d, lam);
+    feynman_combine(U, F, det, ps.pa, ps.pb, re, im);
 }
 
 }  // namespace qmc

@@ -285,6 +285,43 @@ def test_feynman_complex_matches_oracle(env):
     assert cnt[1] == o["signfail"]
 
 
+def _quartic_feynman(d):
+    """deg F = 4 (forces the factor-list form of the complex family)."""
+    base = W.feynman_regular(9, d=d)
+    e4 = np.zeros((1, d), np.int32)
+    e4[0, 0] = 2
+    e4[0, 1] = 2
+    F = W.Polynomial(np.concatenate([base.F.coef, [0.3]]), np.vstack([base.F.exps, e4]))
+    return W.FeynmanLike(base.U, F, base.a, base.b, base.lam, d)
+
+
+@pytest.mark.parametrize("case", ["regular_d5", "like_d8", "like_d12", "quartic_d4", "few_terms_d6"])
+def test_feynman_forms_match_oracle(env, case):
+    """The symmetric-tensor form (deg U <= 2, deg F <= 3, d <= 11, many terms) and the
+    factor-list form (higher degree, d > 11, few terms) against the oracle."""
+    q, torch, dev, tab = env
+    if case == "regular_d5":
+        fl = W.feynman_regular(7)
+    elif case == "like_d8":
+        fl = W.feynman_like(4, d=8)
+    elif case == "like_d12":
+        fl = W.feynman_like(5, d=12)
+    elif case == "quartic_d4":
+        fl = _quartic_feynman(4)
+    else:
+        full = W.feynman_regular(11, d=6)
+        keep = np.arange(6)   # constant, the linear terms
+        fl = W.FeynmanLike(W.Polynomial(full.U.coef[:3], full.U.exps[:3]),
+                           W.Polynomial(full.F.coef[keep], full.F.exps[keep]), 1.0, 2.5, 0.5, 6)
+    n, m = 1021, 4
+    D = O.shifts(21, m, fl.d)
+    z = tab.z_for(n)[:fl.d] if fl.d <= 10 else L.cbc_naive(n, fl.d)[0]
+    res, gre, gim, cnt = _gpu_sums(env, q.Integrand.polynomial(fl), n, z, D, ("korobov", 3))
+    o = O.shift_sums(O.feynman_complex(fl), ("korobov", 3), n, z, D)
+    _compare(gre, gim, o, n, is_complex=True, tol=1e-11)
+    assert cnt[1] == o["signfail"]
+
+
 @pytest.mark.parametrize("d,nu,nf", [(6, 40, 120), (3, 4, 5), (8, 400, 400), (16, 30, 600),
                                      (8, 5, 400), (5, 300, 6)])
 def test_sector_real_matches_oracle(env, d, nu, nf):

@@ -299,8 +299,9 @@ int qmc_batch_autotune(const qmc_batch_item *items, int count, void *workspace,
  * adaptive mode, Sec. 3.3.1, errormode all) and an evaluation budget maxeval, starting
  * at get_next_n(minn).  Each qmc_server_step admits queued requests in arrival order
  * while memory and slots allow (reserving coefficients, shifts and the tile partials of
- * the request's largest admissible lattice), runs every admitted request on its current
- * lattice in one batched launch per integrand family, and then completes requests whose
+ * the request's largest admissible lattice), runs the admitted requests (all of them, or
+ * those chosen within step_evaluations) on their current lattices in one batched launch
+ * per integrand family, and then completes requests whose
  * goal is met or whose budget is spent, moving the others to larger table sizes.  A
  * request's result does not depend on the other requests: it equals qmc_integrate with
  * the same arguments as long as neither needs more shifts than m.
@@ -312,6 +313,12 @@ typedef struct {
     int max_slots;
     uint64_t m;
     qmc_transform transform;
+    /* Evaluations one step may spend (0: every running request each step).  When set, a
+     * step runs the running requests in order of their current lattice's cost divided by
+     * one plus the steps they have waited (shortest first, aged so that none starves),
+     * while the sum of their evaluations stays within the budget (at least one request
+     * per step).  The choice changes when a request runs, never its numbers. */
+    uint64_t step_evaluations;
 } qmc_server_config;
 typedef struct qmc_server qmc_server;
 
@@ -338,6 +345,26 @@ int qmc_server_status(qmc_server *s, uint64_t id, int *state, qmc_result *result
 
 /* Queued and running requests and the free bytes of the pool. */
 int qmc_server_counts(qmc_server *s, int *pending, int *active, size_t *free_bytes);
+
+/* ---- generating vectors: fast CBC on the device -------------------------------------- */
+
+/* Component-by-component construction (App. A.3 of the paper; the fast algorithm of
+ * Nuyens and Cools) of a rank-1 lattice generating vector for a prime number of points n,
+ * in the Korobov space of smoothness alpha = 2 with kernel omega(x) = 2 pi^2 (x^2 - x + 1/6),
+ * product weights gamma and parameter beta: z_1 = 1, then each z_j in 1..(n-1)/2 minimises
+ *   e^2(z_1..z_j) = -1 + (1/n) sum_{k<n} prod_{l<=j} (beta + gamma omega({k z_l / n})).
+ * The candidate sums are cyclic convolutions over the multiplicative group of n, folded to
+ * length (n-1)/2 and evaluated with cuFFT (FP64); sums within 1e-14 omega(0) sum_k p(k) of
+ * the minimum are ties, won by the smallest z.  The shipped tables use gamma = 1/s_max,
+ * beta = 1.
+ * z_out: host, s entries.  e2_out: host, s entries (the squared worst-case error after each
+ * component), or NULL.  stream: NULL = default.  Device memory (about qmc_cbc_device_bytes(n)
+ * plus cuFFT's work area) is allocated here and freed before returning.
+ * Errors: QMC_ERR_ARG (n not a prime in [5, 2^53), s outside 1..1024, beta <= 0,
+ * gamma < 0), QMC_ERR_CUDA (allocation, FFT or launch failure), QMC_ERR_NO_DEVICE. */
+size_t qmc_cbc_device_bytes(uint64_t n);
+int qmc_cbc_korobov(uint64_t n, int s, double gamma, double beta, uint64_t *z_out,
+                    double *e2_out, void *stream);
 
 /* ---- host entry points -------------------------------------------------------------- */
 

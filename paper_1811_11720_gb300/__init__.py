@@ -27,10 +27,13 @@ __all__ = ["QMCError", "lib", "GenvecTable", "Integrand", "make_transform", "get
            "make_shifts", "rule", "points", "sums_workspace_bytes", "sums", "sums_noalloc",
            "finalize",
            "evaluate", "histogram_workspace_bytes", "histogram", "fit_polysingular",
-           "integrate", "integrate_device", "Batch", "Server", "DEFAULT_TABLE"]
+           "integrate", "integrate_device", "Batch", "Server", "cbc_korobov", "DEFAULT_TABLE",
+           "EXTENSION_TABLE"]
 
-DEFAULT_TABLE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
-                             "tables", "cbc_korobov_a2_s10.txt")
+_TABLES = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tables")
+DEFAULT_TABLE = os.path.join(_TABLES, "cbc_korobov_a2_s10.txt")
+# sizes past the CPU-built table, computed with qmc_cbc_korobov (extend_table.py)
+EXTENSION_TABLE = os.path.join(_TABLES, "cbc_korobov_a2_s10_gpu.txt")
 
 _lib = None
 
@@ -86,12 +89,21 @@ class GenvecTable:
                                        int(self.z.shape[1]), int(self.n.shape[0]))
 
     @classmethod
-    def load(cls, path: str = DEFAULT_TABLE) -> "GenvecTable":
-        rows = []
-        with open(path) as fh:
-            for line in fh:
-                if line.strip() and not line.startswith("#"):
-                    rows.append([int(t) for t in line.split()])
+    def load(cls, path: str | None = None, extension: bool = True) -> "GenvecTable":
+        """Rows "n z_1 .. z_s" ('#' comments).  Default: the shipped table plus, when
+        present, its extension to larger n; a size in both keeps the first file's row."""
+        paths = [path or DEFAULT_TABLE]
+        if path is None and extension and os.path.exists(EXTENSION_TABLE):
+            paths.append(EXTENSION_TABLE)
+        rows, seen = [], set()
+        for pth in paths:
+            with open(pth) as fh:
+                for line in fh:
+                    if line.strip() and not line.startswith("#"):
+                        r = [int(t) for t in line.split()]
+                        if r[0] not in seen:
+                            seen.add(r[0])
+                            rows.append(r)
         s = min(len(r) - 1 for r in rows)
         return cls([r[0] for r in rows], [r[1:1 + s] for r in rows])
 
@@ -202,6 +214,19 @@ def get_next_n(table: GenvecTable, preferred: int) -> int:
     out = C.c_uint64()
     _check(lib().qmc_get_next_n(C.byref(table.struct), int(preferred), C.byref(out)), "get_next_n")
     return int(out.value)
+
+
+def cbc_korobov(n: int, s: int, gamma: float | None = None, beta: float = 1.0, stream=None):
+    """Fast CBC generating vector on the device (qmc_cbc_korobov): returns (z, e2), the
+    s components and the squared worst-case error after each.  gamma defaults to 1/s."""
+    z = np.zeros(s, dtype=np.uint64)
+    e2 = np.zeros(s)
+    g = float(gamma) if gamma is not None else (1.0 / s if s > 0 else 0.0)
+    _check(lib().qmc_cbc_korobov(int(n), int(s), g, float(beta),
+                                 z.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                 e2.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)),
+           "cbc_korobov")
+    return z, e2
 
 
 def make_shifts(seed: int, m: int, d: int) -> np.ndarray:
@@ -425,8 +450,9 @@ class Server:
     PENDING, ACTIVE, DONE = 0, 1, 2
 
     def __init__(self, table: GenvecTable, memory_budget: int, max_slots: int, m: int,
-                 transform=("korobov", 3), stream=None):
-        cfg = qmc_server_config(int(memory_budget), int(max_slots), int(m), make_transform(transform))
+                 transform=("korobov", 3), stream=None, step_evaluations: int = 0):
+        cfg = qmc_server_config(int(memory_budget), int(max_slots), int(m), make_transform(transform),
+                                int(step_evaluations))
         h = C.c_void_p()
         _check(lib().qmc_server_create(C.byref(table.struct), C.byref(cfg), _stream(stream),
                                        C.byref(h)), "server_create")

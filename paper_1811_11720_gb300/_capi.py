@@ -70,7 +70,7 @@ class qmc_batch_config(C.Structure):
 
 class qmc_server_config(C.Structure):
     _fields_ = [("memory_budget", C.c_size_t), ("max_slots", C.c_int), ("m", C.c_uint64),
-                ("transform", qmc_transform)]
+                ("transform", qmc_transform), ("step_evaluations", C.c_uint64)]
 
 
 class qmc_fit_opts(C.Structure):
@@ -123,6 +123,9 @@ PROTOTYPES = {
     "qmc_server_status": (C.c_int, [C.c_void_p, C.c_uint64, _P(C.c_int), _P(qmc_result),
                                     _P(C.c_double)]),
     "qmc_server_counts": (C.c_int, [C.c_void_p, _P(C.c_int), _P(C.c_int), _P(C.c_size_t)]),
+    "qmc_cbc_device_bytes": (C.c_size_t, [C.c_uint64]),
+    "qmc_cbc_korobov": (C.c_int, [C.c_uint64, C.c_int, C.c_double, C.c_double, _P(C.c_uint64),
+                                  _P(C.c_double), C.c_void_p]),
     "qmc_integrate": (C.c_int, [_P(qmc_integrand), _P(qmc_genvec_table), C.c_uint64, C.c_uint64,
                                 qmc_transform, _P(qmc_fit_opts), C.c_uint64, _P(qmc_options),
                                 C.c_void_p, _P(qmc_result)]),

@@ -77,7 +77,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     tmp = LIB + f".tmp{os.getpid()}"
     libdir = _cuda_lib_dir(nvcc)
     cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + \
-        ["-Xlinker", f"-rpath,{libdir}"]
+        ["-lcufft", "-Xlinker", f"-rpath,{libdir}"]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.run(cmd, check=True)

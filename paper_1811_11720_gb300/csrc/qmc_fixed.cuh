@@ -2,18 +2,20 @@
 //
 // For Korobov<r,r> the map is phi(v) = v^(r+1) P(v) on v = min(x, 1 - x) in [0, 1/2]
 // (phi(x) = 1 - phi(1 - x) above 1/2), with P(v) = sum_k A_k v^k,
-// A_k = C (-1)^k binom(r,k) / (r+1+k), and the weight is C (v (1 - v))^r.  For r <= 4 every
-// A_k is an integer (3 -2 | 10 -15 6 | 35 -84 70 -20 | 126 -420 540 -315 70), so the map is
-// evaluated with 64-bit integer multiplies, the order r being a compile-time constant:
+// A_k = C (-1)^k binom(r,k) / (r+1+k), and the weight is C (v (1 - v))^r.  In w = 1 - v the
+// polynomial has positive integer coefficients, so for r = 1..4 (compiled orders) the map
+// is evaluated with unsigned 64-bit integer multiplies, r being a compile-time constant:
 //
 //   * v enters in 0.64 fixed point, V = v 2^64, straight from the top word X of the shifted
 //     lattice fraction x: V = X (x < 1/2) or 2^64 - 1 - X, within 2^-64 of min(x, 1 - x).
-//   * P(v) by Horner in signed fixed point with F fractional bits, F the largest value that
-//     keeps every Horner intermediate (bounded on [0, 1/2] by
-//     M = max_k sum_{j>=k} |A_j| 2^(k-j)) below 2^62 / (M + 1); each step truncates by at
-//     most 2^-F.  P decreases on [0, 1/2] from A_0 to 2^r, so P 2^(F+G) < 2^63 after a
-//     further shift by G.
-//   * phi = v^(r+1) P in 0.64 fixed point; the absolute error is below 2^-54 (the power's
+//   * P is evaluated in w = 1 - v, where its coefficients are positive:
+//       P(v) = C int_0^1 s^r (1 - v s)^r ds = sum_k binom(r+k, k) (1 - v)^k
+//     (expand (1 - v s)^r = ((1 - s) + w s)^r and integrate the Beta integrals), e.g.
+//     1 + 2w | 1 + 3w + 6w^2 | 1 + 4w + 10w^2 + 20w^3 | 1 + 5w + 15w^2 + 35w^3 + 70w^4.
+//     Unsigned Horner in fixed point with F fractional bits, F the largest value with
+//     P(0) 2^F = sum_k binom(r+k, k) 2^F < 2^64 (every Horner intermediate is at most that
+//     for w <= 1); each step truncates by at most 2^-F (F = 62, 60, 58, 57 for r = 1..4).
+//   * phi = v^(r+1) P in 0.64 fixed point; the absolute error is below 2^-55 (the power's
 //     truncations times P <= 126, and one truncation of the last product).  The integrands
 //     that accept a fixed-point coordinate take it as is; otherwise it is rounded to double.
 //   * t = v (1 - v) = V - V^2 2^-64 in 0.64 fixed point, normalized into the format Fx (a
@@ -34,49 +36,22 @@ namespace qmc {
 
 // ---------------------------------------------------------------------------------------
 // Compile-time coefficients of Korobov<r,r>.
-__host__ __device__ constexpr long long korobov_C(int r) {   // (2r+1) binom(2r, r)
-    long long c = 2 * r + 1;
-    for (int i = 1; i <= r; ++i) c = c * (r + i) / i;
-    return c;
-}
-__host__ __device__ constexpr long long korobov_A(int r, int k) {   // C (-1)^k binom(r,k) / (r+1+k), exact for r <= 4
-    long long b = 1;
-    for (int i = 1; i <= k; ++i) b = b * (r - k + i) / i;
-    const long long v = korobov_C(r) * b / (r + 1 + k);
-    return (k & 1) ? -v : v;
-}
-__host__ __device__ constexpr bool korobov_exact(int r) {
-    bool ok = true;
-    for (int k = 0; k <= r; ++k) {
-        long long b = 1;
-        for (int i = 1; i <= k; ++i) b = b * (r - k + i) / i;
-        ok = ok && (korobov_C(r) * b) % (r + 1 + k) == 0;
-    }
-    return ok;
-}
 __host__ __device__ constexpr double pow2_c(int e) {
     double x = 1.0;
     for (int i = 0; i < e; ++i) x *= 2.0;
     return x;
 }
-__host__ __device__ constexpr int korobov_F(int r) {   // Horner fractional bits
-    double M = 0.0;
-    for (int k = 0; k <= r; ++k) {
-        double s = 0.0;
-        for (int j = r; j >= k; --j) {
-            const long long a = korobov_A(r, j);
-            s = s * 0.5 + (double)(a < 0 ? -a : a);
-        }
-        if (s > M) M = s;
-    }
-    int F = 0;
-    while ((M + 1.0) * pow2_c(F + 1) <= pow2_c(62)) ++F;
-    return F;
+__host__ __device__ constexpr long long korobov_Pw(int r, int k) {   // binom(r+k, k)
+    long long b = 1;
+    for (int i = 1; i <= k; ++i) b = b * (r + i) / i;
+    return b;
 }
-__host__ __device__ constexpr int korobov_G(int r) {   // extra shift of P before the last product: A_0 2^(F+G) <= 2^62
-    int G = 0;
-    while ((double)korobov_A(r, 0) * pow2_c(korobov_F(r) + G + 1) <= pow2_c(62)) ++G;
-    return G;
+__host__ __device__ constexpr int korobov_F(int r) {   // fractional bits of P in w = 1 - v
+    double S = 0.0;
+    for (int k = 0; k <= r; ++k) S += (double)korobov_Pw(r, k);
+    int F = 0;
+    while (S * pow2_c(F + 1) < pow2_c(64)) ++F;
+    return F;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -128,14 +103,13 @@ __device__ __forceinline__ double fixed_to_double64(uint64_t x) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Horner steps k = K, K-1, ..., 0 of P for Korobov<R,R>: p <- floor(p V / 2^64) + A_k 2^F.
-// For signed p, hi(p_unsigned V) = floor(p V / 2^64) + V [p < 0].
+// Horner steps k = K, K-1, ..., 0 of P(w) = sum_k binom(R+k, k) w^k for Korobov<R,R>:
+// p <- floor(p W / 2^64) + binom(R+k, k) 2^F, W = w 2^64.
 template <int R, int K>
-__device__ __forceinline__ long long korobov_horner(long long p, uint64_t V) {
-    constexpr long long a = korobov_A(R, K) * (1ll << korobov_F(R));
-    const uint64_t hi = __umul64hi((uint64_t)p, V) - (p < 0 ? V : 0ull);
-    p = (long long)hi + a;
-    if constexpr (K > 0) return korobov_horner<R, K - 1>(p, V);
+__device__ __forceinline__ uint64_t korobov_horner(uint64_t p, uint64_t W) {
+    constexpr uint64_t c = (uint64_t)korobov_Pw(R, K) << korobov_F(R);
+    p = __umul64hi(p, W) + c;
+    if constexpr (K > 0) return korobov_horner<R, K - 1>(p, W);
     else return p;
 }
 
@@ -143,11 +117,11 @@ __device__ __forceinline__ long long korobov_horner(long long p, uint64_t V) {
 // running product Wp.
 template <int R>
 __device__ __forceinline__ uint64_t korobov_phi_fixed(uint64_t V, Fx &Wp) {
-    static_assert(R >= 1 && R <= kMaxKorobovInt && korobov_exact(R), "integer Korobov order");
+    static_assert(R >= 1 && R <= kMaxKorobovInt, "integer Korobov order");
     constexpr int F = korobov_F(R);
-    constexpr int G = korobov_G(R);
-    constexpr long long top = korobov_A(R, R) * (1ll << F);
-    const long long p = korobov_horner<R, R - 1>(top, V);
+    constexpr uint64_t top = (uint64_t)korobov_Pw(R, R) << F;
+    // w = 1 - v: 2^64 - 1 - V, within 2^-64 of (1 - v) 2^64
+    const uint64_t p = korobov_horner<R, R - 1>(top, ~V);
     // v^(r+1) 2^64
     const uint64_t V2 = __umul64hi(V, V);
     uint64_t pw;
@@ -157,7 +131,7 @@ __device__ __forceinline__ uint64_t korobov_phi_fixed(uint64_t V, Fx &Wp) {
     else pw = __umul64hi(__umul64hi(V2, V2), V);
     // t = v - v^2 in 0.64 fixed point (<= 2^62), into the weight product
     Wp = fx_norm(fx_mul(Wp, fx_norm_any(V - V2, 0)));
-    return __umul64hi(pw, (uint64_t)p << G) << (64 - F - G);
+    return __umul64hi(pw, p) << (64 - F);
 }
 
 // C^d (prod_j t_j)^r rounded to double; cdx = C^d as Fx.

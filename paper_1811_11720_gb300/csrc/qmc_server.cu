@@ -58,6 +58,7 @@ struct Request {
     std::vector<uint64_t> shifts;
     // progress
     uint64_t n = 0, evaluations = 0, iterations = 0;
+    uint64_t waited = 0;     // steps spent waiting since the request last ran
     unsigned long long nonfinite = 0, signfail = 0;
     double res[4] = {0, 0, 0, 0};
     double t_submit = 0, t_done = 0;
@@ -330,22 +331,54 @@ extern "C" int qmc_server_step(qmc_server *s, int *completed) {
         if (completed) *completed = done;
         return QMC_OK;
     }
-    // 2. one batched launch per family over all active requests
+    // 2. the requests of this step: all, or shortest (aged) first within the budget
+    std::vector<uint64_t> run = s->active, idle;
+    if (s->cfg.step_evaluations) {
+        std::vector<std::pair<double, size_t>> key;
+        for (size_t q = 0; q < s->active.size(); ++q) {
+            const Request &r = s->reqs[s->active[q]];
+            key.push_back({(double)r.n * (double)s->cfg.m / (1.0 + (double)r.waited), q});
+        }
+        std::stable_sort(key.begin(), key.end());
+        run.clear();
+        uint64_t spent = 0;
+        size_t nchosen = 0;
+        std::vector<char> chosen(s->active.size(), 0);
+        for (const auto &kv : key) {
+            const Request &r = s->reqs[s->active[kv.second]];
+            const uint64_t cost = r.n * s->cfg.m;
+            if (nchosen && spent + cost > s->cfg.step_evaluations) continue;
+            spent += cost;
+            chosen[kv.second] = 1;
+            ++nchosen;
+        }
+        for (size_t q = 0; q < s->active.size(); ++q) {
+            Request &r = s->reqs[s->active[q]];
+            if (chosen[q]) {
+                run.push_back(r.id);
+                r.waited = 0;
+            } else {
+                idle.push_back(r.id);
+                ++r.waited;
+            }
+        }
+    }
+    // one batched launch per family over the requests of this step
     std::vector<int> fams;
-    for (uint64_t id : s->active) {
+    for (uint64_t id : run) {
         int fam = s->reqs[id].fh.family;
         if (std::find(fams.begin(), fams.end(), fam) == fams.end()) fams.push_back(fam);
     }
     const int m = (int)s->cfg.m;
     const int spb = std::max(1, kSumsThreads / m);
-    if (cudaMemsetAsync(s->d_counters, 0, sizeof(unsigned long long) * 2 * s->active.size(), s->stream) != cudaSuccess)
+    if (cudaMemsetAsync(s->d_counters, 0, sizeof(unsigned long long) * 2 * run.size(), s->stream) != cudaSuccess)
         return QMC_ERR_CUDA;
     std::vector<uint64_t> order;   // request id per batch slot
     size_t base = 0;
     for (int fam : fams) {
         const size_t g0 = base;
         uint64_t tiles = 0;
-        for (uint64_t id : s->active) {
+        for (uint64_t id : run) {
             Request &r = s->reqs[id];
             if (r.fh.family != fam) continue;
             qmc_batch_item b;
@@ -383,7 +416,7 @@ extern "C" int qmc_server_step(qmc_server *s, int *completed) {
         cudaStreamSynchronize(s->stream) != cudaSuccess)
         return QMC_ERR_CUDA;
     // 3. goals, escalation, completion
-    std::vector<uint64_t> still;
+    std::vector<uint64_t> still = idle;
     const double t = now_s();
     for (size_t q = 0; q < na; ++q) {
         Request &r = s->reqs[order[q]];

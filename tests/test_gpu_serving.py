@@ -88,6 +88,35 @@ def test_memory_budget_limits_concurrency(env):
     assert most == 2
 
 
+def test_step_budget_runs_short_requests_first(env):
+    """With a per-step evaluation budget a short request that arrives behind a long one
+    completes first, and both results equal those of the unbudgeted server."""
+    q, torch, tab = env
+    c, w = W.genz_params(4, 5, 8)
+    short = q.Integrand.genz(4, c, w)
+    results = {}
+    for budget in (0, 1 << 20):
+        srv = q.Server(tab, memory_budget=256 << 20, max_slots=8, m=16, step_evaluations=budget)
+        big = srv.submit(_feyn(q, 2), epsrel=1e-12, maxeval=60_000_000, seed=4)
+        srv.step()
+        small = srv.submit(short, epsrel=1e-4, maxeval=10_000_000, seed=5)
+        done_at = {}
+        for step in range(400):
+            for rid in (big, small):
+                if rid not in done_at and srv.status(rid)["state"] == srv.DONE:
+                    done_at[rid] = step
+            if len(done_at) == 2:
+                break
+            srv.step()
+        assert len(done_at) == 2
+        results[budget] = (srv.status(big), srv.status(small), done_at[small] < done_at[big])
+        srv.close()
+    for k in ("integral", "error", "n", "evaluations"):
+        assert results[0][0][k] == results[1 << 20][0][k], k
+        assert results[0][1][k] == results[1 << 20][1][k], k
+    assert results[1 << 20][2]
+
+
 def test_server_rejects_bad_arguments(env):
     q, torch, tab = env
     with pytest.raises(q.QMCError) as e:

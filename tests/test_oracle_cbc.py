@@ -116,6 +116,27 @@ def test_rank1_lattice_integrates_trig_exactly_for_table(genvec_table):
         prev = e
 
 
+def test_extension_table_file():
+    """The GPU-built rows beyond the CPU table: the paper's remaining sizes up to 2^31 - 1,
+    well-formed vectors, and the whole size rule covered by the two files together."""
+    ext = os.path.join(os.path.dirname(TABLE), "cbc_korobov_a2_s10_gpu.txt")
+    rows = O.load_genvec_table(ext)
+    main = O.load_genvec_table(TABLE)
+    sizes = L.lattice_sizes()
+    assert sorted(set(rows) | set(main)) == sorted(sizes)
+    assert min(rows) > max(main)
+    for n, z in rows.items():
+        assert L.is_prime(n)
+        assert len(z) == 10 and z[0] == 1
+        assert all(0 < v <= (n - 1) // 2 for v in z)
+
+
+def test_extension_size_rule_matches_oracle():
+    """The package's own size rule (used to extend the table) equals the oracle's."""
+    from paper_1811_11720_gb300.extend_table import table_sizes
+    assert table_sizes() == L.lattice_sizes()
+
+
 def test_loader_roundtrip(tmp_path):
     p = tmp_path / "t.txt"
     p.write_text("# x\n7 1 3\n11 1 7\n")

@@ -455,7 +455,8 @@ def run_serve_workload(args):
     out = {"metric": "served integrals/s", "unit": "integrals/s", "higher_is_better": True,
            "n_gpus": 1, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "feynman_regular_d5_beta0.6|0.95_lam1_korobov3_m32_eps1e-8..1e-3_poisson",
-                      "requests": N, "maxeval": args.serve_maxeval}, "rates": []}
+                      "requests": N, "maxeval": args.serve_maxeval,
+                      "step_evaluations": int(args.serve_step_evals)}, "rates": []}
 
     def arrivals(rate):
         r = np.random.default_rng(args.seed + int(rate * 1000))
@@ -464,7 +465,8 @@ def run_serve_workload(args):
     for rate in args.rates:
         t_arr = arrivals(rate)
         # continuous batching
-        srv = q.Server(table, memory_budget=int(args.serve_budget), max_slots=256, m=M_SHIFTS)
+        srv = q.Server(table, memory_budget=int(args.serve_budget), max_slots=256, m=M_SHIFTS,
+                       step_evaluations=int(args.serve_step_evals))
         ids = [None] * N
         done_t = [None] * N
         t0 = time.perf_counter()
@@ -571,6 +573,8 @@ def main():
     ap.add_argument("--rates", type=float, nargs="*", default=[2.0, 8.0, 32.0])
     ap.add_argument("--serve-maxeval", type=float, default=3.2e7)
     ap.add_argument("--serve-budget", type=float, default=4e9)
+    ap.add_argument("--serve-step-evals", type=float, default=2.0 ** 25,
+                    help="server step budget in evaluations (0: all running requests each step)")
     ap.add_argument("--batch-count", type=int, default=2000)
     ap.add_argument("--batch-nmax", type=float, default=1e5)
     args = ap.parse_args()

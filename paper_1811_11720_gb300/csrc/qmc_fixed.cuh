@@ -14,15 +14,16 @@
 //     1 + 2w | 1 + 3w + 6w^2 | 1 + 4w + 10w^2 + 20w^3 | 1 + 5w + 15w^2 + 35w^3 + 70w^4.
 //     Unsigned Horner in fixed point with F fractional bits, F the largest value with
 //     P(0) 2^F = sum_k binom(r+k, k) 2^F < 2^64 (every Horner intermediate is at most that
-//     for w <= 1); each step truncates by at most 2^-F (F = 62, 60, 58, 57 for r = 1..4).
-//   * phi = v^(r+1) P in 0.64 fixed point; the absolute error is below 2^-55 (the power's
-//     truncations times P <= 126, and one truncation of the last product).  The integrands
+//     for w <= 1); each step truncates by at most 3 units of 2^-F (F = 62, 60, 58, 57 for
+//     r = 1..4; the products drop their low partial products, see mulhi_trunc).
+//   * phi = v^(r+1) P in 0.64 fixed point; the absolute error is below 2^-54 (the power's
+//     truncations times P <= 126, and the truncations of the last product).  The integrands
 //     that accept a fixed-point coordinate take it as is; otherwise it is rounded to double.
 //   * t = v (1 - v) = V - V^2 2^-64 in 0.64 fixed point, normalized into the format Fx (a
 //     64-bit mantissa and an exponent) for the running product over the dimensions, whose
 //     r-th power times C^d is rounded once to double: the product keeps relative precision
-//     however small it becomes, and each t is exact to 2^-64 absolutely, which moves the
-//     weight by less than 2^-60 of its largest value C^d 4^(-rd).
+//     however small it becomes, and each t is exact to 3 2^-64 absolutely, which moves the
+//     weight by less than 2^-58 of its largest value C^d 4^(-rd).
 //
 // GB300 runs ~2 FP64 fused multiply-adds per clock per SM but ~32x as many 32-bit integer
 // multiply-adds, so the ~8 FP64 instructions per dimension of the FP64 form cost more than
@@ -55,6 +56,17 @@ __host__ __device__ constexpr int korobov_F(int r) {   // fractional bits of P i
 }
 
 // ---------------------------------------------------------------------------------------
+// High word of a 64 x 64-bit product without the low x low partial product and the low
+// halves of the cross products: a 32 x 32 -> 64-bit multiply, two 32-bit high multiplies
+// and a 64-bit add.  The result is at most 2 below floor(a b / 2^64) (never above), which
+// the fixed-point error bounds below include.
+__device__ __forceinline__ uint64_t mulhi_trunc(uint64_t a, uint64_t b) {
+    const uint32_t al = (uint32_t)a, ah = (uint32_t)(a >> 32);
+    const uint32_t bl = (uint32_t)b, bh = (uint32_t)(b >> 32);
+    return (uint64_t)ah * bh + __umulhi(ah, bl) + __umulhi(al, bh);
+}
+
+// ---------------------------------------------------------------------------------------
 // value = m 2^(e - 64); m == 0 encodes zero.  Normalized: m >= 2^63.
 struct Fx {
     uint64_t m;
@@ -67,8 +79,8 @@ __device__ __forceinline__ Fx fx_of_double(double v) {
     return {b ? ((b << 11) | 0x8000000000000000ull) : 0ull, (int)(b >> 52) - 1022};
 }
 
-// Truncated product; exponents add.
-__device__ __forceinline__ Fx fx_mul(Fx a, Fx b) { return {__umul64hi(a.m, b.m), a.e + b.e}; }
+// Truncated product (relative error below 2^-61 for normalized inputs); exponents add.
+__device__ __forceinline__ Fx fx_mul(Fx a, Fx b) { return {mulhi_trunc(a.m, b.m), a.e + b.e}; }
 
 // Normalize a mantissa that is zero or >= 2^32 (shift 0..32; zero stays zero).
 __device__ __forceinline__ Fx fx_norm(Fx a) {
@@ -76,8 +88,14 @@ __device__ __forceinline__ Fx fx_norm(Fx a) {
     return {a.m << lz, a.e - lz};
 }
 
-// Normalize any mantissa (zero stays zero).
+// Normalize any mantissa (zero stays zero).  Mantissas below 2^32 (a lattice coordinate
+// within 2^-32 of 0 or 1) take the slower branch.
 __device__ __forceinline__ Fx fx_norm_any(uint64_t m, int e) {
+    const uint32_t hi = (uint32_t)(m >> 32);
+    if (hi) {
+        const int lz = __clz(hi);
+        return {m << lz, e - lz};
+    }
     const int lz = __clzll(m);   // 64 for zero
     return {m ? (m << (lz & 63)) : 0ull, e - lz};
 }
@@ -108,7 +126,7 @@ __device__ __forceinline__ double fixed_to_double64(uint64_t x) {
 template <int R, int K>
 __device__ __forceinline__ uint64_t korobov_horner(uint64_t p, uint64_t W) {
     constexpr uint64_t c = (uint64_t)korobov_Pw(R, K) << korobov_F(R);
-    p = __umul64hi(p, W) + c;
+    p = mulhi_trunc(p, W) + c;
     if constexpr (K > 0) return korobov_horner<R, K - 1>(p, W);
     else return p;
 }
@@ -123,15 +141,15 @@ __device__ __forceinline__ uint64_t korobov_phi_fixed(uint64_t V, Fx &Wp) {
     // w = 1 - v: 2^64 - 1 - V, within 2^-64 of (1 - v) 2^64
     const uint64_t p = korobov_horner<R, R - 1>(top, ~V);
     // v^(r+1) 2^64
-    const uint64_t V2 = __umul64hi(V, V);
+    const uint64_t V2 = mulhi_trunc(V, V);
     uint64_t pw;
     if constexpr (R == 1) pw = V2;
-    else if constexpr (R == 2) pw = __umul64hi(V2, V);
-    else if constexpr (R == 3) pw = __umul64hi(V2, V2);
-    else pw = __umul64hi(__umul64hi(V2, V2), V);
+    else if constexpr (R == 2) pw = mulhi_trunc(V2, V);
+    else if constexpr (R == 3) pw = mulhi_trunc(V2, V2);
+    else pw = mulhi_trunc(mulhi_trunc(V2, V2), V);
     // t = v - v^2 in 0.64 fixed point (<= 2^62), into the weight product
     Wp = fx_norm(fx_mul(Wp, fx_norm_any(V - V2, 0)));
-    return __umul64hi(pw, p) << (64 - F);
+    return mulhi_trunc(pw, p) << (64 - F);
 }
 
 // C^d (prod_j t_j)^r rounded to double; cdx = C^d as Fx.

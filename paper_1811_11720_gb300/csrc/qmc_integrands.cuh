@@ -16,6 +16,7 @@
 #pragma once
 #include <cstdint>
 
+#include "qmc_exp.cuh"
 #include "qmc_fp.cuh"
 #include "qmc_params.cuh"
 #include "qmc_poly.cuh"
@@ -29,13 +30,12 @@ namespace qmc {
 //     partial sum of c_j x_j (or c_j |x_j - w_j|) stays below 2^63;
 //   Gaussian (4): cq_j = c_j 2^S with S = 61 - floor(log2 max_j c_j), so |c_j (x_j - w_j)|
 //     2^S < 2^62 and each square (2^(2S - 64) scale) is below 2^60.
-// Each term truncates by at most one unit (2^-S, or 2^(64 - 2S) for squares); the forms
+// Each term truncates by at most three units (2^-S, or 2^(64 - 2S) for squares); the forms
 // are therefore exact to ~2^-56 absolutely for the benchmark's c (||c||_1 <= 18).  ok is
 // false (double path) unless every c_j >= 0 and 0 <= w_j <= 1.
 struct FixedForms {
     uint64_t cl[kMaxDim];
-    int64_t cq[kMaxDim];
-    int64_t w63[kMaxDim];    // w_j 2^63, at most 2^63 - 1
+    uint64_t cq[kMaxDim];
     uint64_t w64[kMaxDim];   // w_j 2^64, at most 2^64 - 1
     int S;
     bool ok;
@@ -50,6 +50,7 @@ struct FamilyShared {
     double sub_hi[256];     // the same for j = 8 + bit
     double s0;
     int64_t h[kMaxDim];
+    double exp2t[32];       // 2^(j/32) for exp_table (families with an exponential)
     FixedForms fx;
     PolyShared poly;
 };
@@ -88,8 +89,7 @@ __device__ __forceinline__ void stage_fixed_forms(const P &p, FixedForms &fx) {
         const double c = p.c[tid];
         const double w = p.w ? p.w[tid] : 0.0;
         fx.cl[tid] = __double2ull_rz(ldexp(c, S));
-        fx.cq[tid] = __double2ll_rz(ldexp(c, S));
-        fx.w63[tid] = w >= 1.0 ? 0x7FFFFFFFFFFFFFFFll : __double2ll_rz(ldexp(w, 63));
+        fx.cq[tid] = __double2ull_rz(ldexp(c, S));
         fx.w64[tid] = w >= 1.0 ? 0xFFFFFFFFFFFFFFFFull : __double2ull_rz(ldexp(w, 64));
     }
     if (tid == 0) {
@@ -132,6 +132,10 @@ __device__ __forceinline__ void stage_family(const P &p, FamilyShared &fs) {
             }
         }
         if constexpr (kHasFixedForm<FAM>) stage_fixed_forms<FAM>(p, fs.fx);
+        if constexpr (FAM == QMC_GENZ_GAUSSIAN || FAM == QMC_GENZ_C0 ||
+                      FAM == QMC_GENZ_DISCONTINUOUS) {
+            if (tid < 32) fs.exp2t[tid] = kExp2Table[tid];
+        }
     }
 }
 
@@ -165,7 +169,7 @@ struct FamilyAcc<QMC_GENZ_OSCILLATORY> {
     uint64_t sl;
     __device__ __forceinline__ void init_fixed() { sl = 0; }
     __device__ __forceinline__ void add_fixed(int j, uint64_t x, const FamilyShared &fs) {
-        sl += __umul64hi(x, fs.fx.cl[j]);
+        sl += mulhi_trunc(x, fs.fx.cl[j]);
     }
     __device__ __forceinline__ void finish_fixed(int, const FamilyShared &fs, double &re,
                                                  double &im, unsigned long long &) {
@@ -212,7 +216,7 @@ struct FamilyAcc<QMC_GENZ_CORNER_PEAK> {
     uint64_t sl;
     __device__ __forceinline__ void init_fixed() { sl = 0; }
     __device__ __forceinline__ void add_fixed(int j, uint64_t x, const FamilyShared &fs) {
-        sl += __umul64hi(x, fs.fx.cl[j]);
+        sl += mulhi_trunc(x, fs.fx.cl[j]);
     }
     __device__ __forceinline__ void finish_fixed(int d, const FamilyShared &fs, double &re,
                                                  double &im, unsigned long long &) {
@@ -237,17 +241,18 @@ struct FamilyAcc<QMC_GENZ_GAUSSIAN> {
         re = exp(-s);
         im = 0.0;
     }
-    // fixed point: q = c (x - w) 2^S (|q| < 2^62), q^2 2^(2S - 64) < 2^60, summed in 64 bits
+    // fixed point: q = c |x - w| 2^S < 2^62, q^2 2^(2S - 64) < 2^60, summed in 64 bits
     uint64_t sq;
     __device__ __forceinline__ void init_fixed() { sq = 0; }
     __device__ __forceinline__ void add_fixed(int j, uint64_t x, const FamilyShared &fs) {
-        const long long diff = (long long)(x >> 1) - fs.fx.w63[j];      // (x - w) 2^63
-        const long long q = __mul64hi(diff, fs.fx.cq[j]) * 2;           // c (x - w) 2^S
-        sq += (uint64_t)__mul64hi(q, q);
+        const uint64_t w = fs.fx.w64[j];
+        const uint64_t a = x >= w ? x - w : w - x;                       // |x - w| 2^64
+        const uint64_t q = mulhi_trunc(a, fs.fx.cq[j]);                 // c |x - w| 2^S
+        sq += mulhi_trunc(q, q);
     }
     __device__ __forceinline__ void finish_fixed(int, const FamilyShared &fs, double &re,
                                                  double &im, unsigned long long &) {
-        re = exp(-scaled_fixed(sq, 2 * fs.fx.S - 64));
+        re = exp_table(-scaled_fixed(sq, 2 * fs.fx.S - 64), fs.exp2t);
         im = 0.0;
     }
 };
@@ -270,13 +275,13 @@ struct FamilyAcc<QMC_GENZ_C0> {
     uint64_t sl;
     __device__ __forceinline__ void init_fixed() { sl = 0; }
     __device__ __forceinline__ void add_fixed(int j, uint64_t x, const FamilyShared &fs) {
-        const long long diff = (long long)(x >> 1) - fs.fx.w63[j];      // (x - w) 2^63
-        const uint64_t a = (uint64_t)(diff < 0 ? -diff : diff) << 1;    // |x - w| 2^64
-        sl += __umul64hi(a, fs.fx.cl[j]);
+        const uint64_t w = fs.fx.w64[j];
+        const uint64_t a = x >= w ? x - w : w - x;                       // |x - w| 2^64
+        sl += mulhi_trunc(a, fs.fx.cl[j]);
     }
     __device__ __forceinline__ void finish_fixed(int, const FamilyShared &fs, double &re,
                                                  double &im, unsigned long long &) {
-        re = exp(-scaled_fixed(sl, fs.fx.S));
+        re = exp_table(-scaled_fixed(sl, fs.fx.S), fs.exp2t);
         im = 0.0;
     }
 };
@@ -305,11 +310,11 @@ struct FamilyAcc<QMC_GENZ_DISCONTINUOUS> {
     __device__ __forceinline__ void init_fixed() { sl = 0; zero = false; }
     __device__ __forceinline__ void add_fixed(int j, uint64_t x, const FamilyShared &fs) {
         if (j < 2) zero |= x > fs.fx.w64[j];
-        sl += __umul64hi(x, fs.fx.cl[j]);
+        sl += mulhi_trunc(x, fs.fx.cl[j]);
     }
     __device__ __forceinline__ void finish_fixed(int, const FamilyShared &fs, double &re,
                                                  double &im, unsigned long long &) {
-        re = zero ? 0.0 : exp(scaled_fixed(sl, fs.fx.S));
+        re = zero ? 0.0 : exp_table(scaled_fixed(sl, fs.fx.S), fs.exp2t);
         im = 0.0;
     }
 };

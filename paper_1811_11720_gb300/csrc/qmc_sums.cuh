@@ -239,8 +239,15 @@ __device__ __forceinline__ void tile_partial(double acc_re, double acc_im, doubl
     __syncthreads();
 }
 
+// Blocks per SM the register allocation must allow: five for the separable families (48
+// registers; their throughput depends on hiding integer latency), no constraint for the
+// polynomial families (their per-thread working set needs the registers).
+template <int FAM>
+constexpr int kSumsMinBlocks = (FAM == QMC_SECTOR || FAM == QMC_FEYNMAN) ? 1 : 5;
+
 template <int FAM, int TK>
-__global__ void __launch_bounds__(kSumsThreads) sums_kernel(const __grid_constant__ SumsParams p) {
+__global__ void __launch_bounds__(kSumsThreads, kSumsMinBlocks<FAM>)
+    sums_kernel(const __grid_constant__ SumsParams p) {
     __shared__ FamilyShared fsh;
     __shared__ double s_fit[kMaxDim * kFitStride];
     __shared__ double s_red[2 * kSumsThreads];

@@ -48,6 +48,12 @@ M_SHIFTS = 32
 SM_COUNT = 152
 FP64_FLOP_PER_CLK_SM = 4      # 2 DFMA/clk/SM: nominal 1.25 TFLOP/s / (152 SM x 2.07 GHz x 2)
 SM_MAX_MHZ = 2070.0
+# DRAM bytes (read + write) of one lattice-sum launch from the ncu capture of the current
+# kernel (profiles/sums_kernel_gauss_d10_korobov3_n1072187_m32.md: Gaussian, d = 10,
+# Korobov-3, n = 1,072,187).  The kernel reads kilobytes of constants and writes the tile
+# partials, whose number does not grow with n (about 4096 tiles), so the figure applies
+# to the benchmark's launches as measured.  None once the kernel changes.
+TRAFFIC_BYTES_PER_LAUNCH = 250_880
 
 
 def fp64_flops_per_eval(family: int, transform, d: int) -> int:
@@ -643,7 +649,8 @@ def main():
         flops_per_launch = r["flops_per_step"] / len(r["items"])
         achieved = flops_per_launch / (r["kernel_ms_per_launch"] / 1e3) / 1e9
         roof = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak_max, 1),
-                "unit": "GFLOP/s", "frac": round(achieved / peak_max, 4), "traffic": None,
+                "unit": "GFLOP/s", "frac": round(achieved / peak_max, 4),
+                "traffic": TRAFFIC_BYTES_PER_LAUNCH if args.workload == "genz" else None,
                 "peak_at_median_clock": round(SM_COUNT * FP64_FLOP_PER_CLK_SM * sm_mhz / 1e3, 1),
                 "kernel": "sums_kernel (+ tile reduction, <0.1%)",
                 "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2070 MHz",

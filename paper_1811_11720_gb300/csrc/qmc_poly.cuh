@@ -387,9 +387,36 @@ __device__ __forceinline__ cplx feynman_jacobian_det(const double *x, const doub
     return det;
 }
 
+// Principal square root: Re >= 0, the sign of Im from Im a (so a = -x - 0i maps to the
+// lower side of the cut, as exp(Log(a) / 2) with the arg in (-pi, pi] and signed zeros).
+// The branch that avoids cancellation: t = sqrt((|a| + |Re a|) / 2), the other part
+// Im a / (2 t).
+__device__ __forceinline__ cplx csqrt_principal(cplx a) {
+    const double r = hypot(a.re, a.im);
+    if (r == 0.0) return {0.0, a.im};
+    const double t = sqrt(0.5 * (r + fabs(a.re)));
+    const double o = a.im / (2.0 * t);
+    if (a.re >= 0.0) return {t, o};
+    return {fabs(o), copysign(t, a.im)};
+}
+
 // U^a F^-b det for principal branches: exp(a Log U - b Log F) det (a = 1: U exp(-b Log F)).
+// For a = 1 and a half-integer b = n + 1/2 <= 8, F^-b = 1 / (F^n sqrt(F)) with the principal
+// root, the same branch as exp(-b Log F): two square roots and a reciprocal instead of a
+// logarithm, an arctangent, an exponential and a sine/cosine pair.
 __device__ __forceinline__ void feynman_combine(cplx U, cplx F, cplx det, double pa, double pb,
                                                 double &re, double &im) {
+    const double twob = 2.0 * pb;
+    if (pa == 1.0 && pb > 0.0 && pb <= 8.0 && twob == floor(twob) && fmod(twob, 2.0) == 1.0) {
+        cplx den = csqrt_principal(F);
+        const int nint = (int)(pb - 0.5);
+#pragma unroll 1
+        for (int q = 0; q < nint; ++q) den = cmul(den, F);
+        cplx v = cmul(cmul(U, crecip(den)), det);
+        re = v.re;
+        im = v.im;
+        return;
+    }
     const cplx lf = clog_principal(F);
     double er = -pb * lf.re, ei = -pb * lf.im;
     if (pa != 1.0) {

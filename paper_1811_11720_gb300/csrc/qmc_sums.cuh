@@ -3,9 +3,12 @@
 // Work decomposition.  The i-range [i_begin, i_end) is cut into tiles of spb * L points;
 // a block of spb * m threads owns one tile at a time (tiles are dealt round-robin to a
 // persistent grid).  Thread (s, k) evaluates shift k on the L consecutive points of
-// stream s, so the 32 lanes of a warp are 32 shifts of the same points when m = 32: the
-// integer lattice state is identical across the warp and the FP64 instruction stream is
-// uniform.  Each thread accumulates its L samples in FP64; the tile's per-shift partial is
+// stream s, so the 32 lanes of a warp are 32 shifts of the same points when m is a
+// multiple of 32: the lattice state is shared across the warp (see stream_sums) and the
+// instruction stream is uniform.  The transform and, where the integrand allows, the
+// integrand's linear and quadratic forms run in integer fixed point (qmc_fixed.cuh,
+// qmc_integrands.cuh); FP64 is left to the integrand's final function and the sums.
+// Each thread accumulates its L samples in FP64; the tile's per-shift partial is
 // the Neumaier-compensated sum over its spb streams in fixed order, written to
 // partials[tile][k].  Tiles depend only on the i-range, so the result is bit-identical for
 // any grid size, and sharding on tile boundaries reproduces the same partials.

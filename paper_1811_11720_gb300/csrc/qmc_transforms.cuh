@@ -1,10 +1,13 @@
 // qmc_transforms.cuh -- periodizing transforms (Sec. 2.3) and the PolySingular
 // variance-reduction map (Sec. 2.4, Eq. (ISfit)) as device functions.
 //
-// FP64 is the bottleneck on GB300, so every step that is exact in integer arithmetic is
+// FP64 is the scarce unit on GB300, so every step that is exact in integer arithmetic is
 // done on the integer pipe: comparisons of non-negative doubles are integer comparisons
 // of their bit patterns, 1 - u for u >= 1/2 (exact by Sterbenz' lemma) and multiplication
-// by 2 are bit manipulations.
+// by 2 are bit manipulations.  The symmetric Korobov maps r <= 4, baker and the identity
+// also have a fixed-point form (transform_fixed; Korobov in qmc_fixed.cuh) that hands the
+// integrand x in 0.64 fixed point; the FP64 forms here serve the other transforms, the
+// fitted rules and the integrands without a fixed-point form.
 //
 // A transform returns the mapped coordinate in reflected form: x = y (refl == false) or
 // x = 1 - y (refl == true), with y <= 1/2 for the symmetric maps.  Evaluating the Korobov

@@ -346,6 +346,38 @@ int qmc_server_status(qmc_server *s, uint64_t id, int *state, qmc_result *result
 /* Queued and running requests and the free bytes of the pool. */
 int qmc_server_counts(qmc_server *s, int *pending, int *active, size_t *free_bytes);
 
+/* ---- tile-aligned sharding --------------------------------------------------------- */
+
+/* qmc_sums cuts an i-range into tiles that depend only on the range's length and m (one
+ * shift group, m <= 256) and folds the per-tile partial sums in tile order in double-double.
+ * A range split at tile boundaries, its tiles' partials gathered in tile order and folded
+ * by qmc_reduce_tiles gives the per-shift sums of qmc_sums bit for bit (Sec. 2.1: the
+ * points of one rule are independent, so shards need no other exchange). */
+
+/* Number of tiles of the decomposition of an i-range of range_len points with m shifts,
+ * and the points per tile (the last tile may be shorter).  Errors: QMC_ERR_ARG,
+ * QMC_ERR_M (m outside 1..256). */
+int qmc_sums_tile_count(uint64_t range_len, uint64_t m, uint64_t *tiles,
+                        uint64_t *points_per_tile);
+
+/* Per-tile partial sums of tiles [tile_begin, tile_end) of the decomposition of
+ * [i_begin, i_end): partials[t][k] = (sum, compensation) of shift k over tile
+ * tile_begin + t, for t < T = tile_end - tile_begin, then (complex family) the same T x m
+ * block for the imaginary part.  partials: device, 2 m T doubles (4 m T complex), written
+ * entirely.  counters: as qmc_sums.  The values equal those qmc_sums forms for the same
+ * tiles.  Errors: as qmc_sums; QMC_ERR_M (m > 256); QMC_ERR_RANGE (empty or out-of-range
+ * tile range). */
+int qmc_sums_tiles(const qmc_integrand *f, const qmc_rule *rule, uint64_t i_begin,
+                   uint64_t i_end, uint64_t tile_begin, uint64_t tile_end, double *partials,
+                   unsigned long long *counters, void *stream);
+
+/* The fold qmc_sums applies to its tiles: sums[2k], sums[2k+1] = double-double sum of shift
+ * k's partials over the tiles in order (complex: the imaginary part at sums[2m + 2k..]).
+ * partials: device, the layout of qmc_sums_tiles for `tiles` tiles.  sums: device, 2 m
+ * (4 m complex) doubles.  Errors: QMC_ERR_ARG, QMC_ERR_M, QMC_ERR_CUDA. */
+int qmc_reduce_tiles(const double *partials, uint64_t tiles, uint64_t m, int is_complex,
+                     double *sums, void *stream);
+
 /* ---- generating vectors: fast CBC on the device -------------------------------------- */
 
 /* Component-by-component construction (App. A.3 of the paper; the fast algorithm of

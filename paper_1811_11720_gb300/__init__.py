@@ -25,6 +25,7 @@ from ._capi import (FAMILY, QMC_MAX_DIM, STATUS, TRANSFORM, qmc_batch_config, qm
 
 __all__ = ["QMCError", "lib", "GenvecTable", "Integrand", "make_transform", "get_next_n",
            "make_shifts", "rule", "points", "sums_workspace_bytes", "sums", "sums_noalloc",
+           "sums_tile_count", "sums_tiles", "reduce_tiles",
            "finalize",
            "evaluate", "histogram_workspace_bytes", "histogram", "fit_polysingular",
            "integrate", "integrate_device", "Batch", "Server", "cbc_korobov", "DEFAULT_TABLE",
@@ -266,6 +267,31 @@ def sums(f: qmc_integrand, r: qmc_rule, i_begin: int, i_end: int, workspace, out
     nbytes = workspace.numel() * workspace.element_size()
     _check(lib().qmc_sums(C.byref(f), C.byref(r), int(i_begin), int(i_end), _ptr(workspace), nbytes,
                           _ptr(out), _ptr(counters), _stream(stream)), "sums")
+    return out
+
+
+def sums_tile_count(range_len: int, m: int) -> tuple[int, int]:
+    """qmc_sums_tile_count: (tiles, points per tile) of qmc_sums' decomposition."""
+    t, ppt = C.c_uint64(), C.c_uint64()
+    _check(lib().qmc_sums_tile_count(int(range_len), int(m), C.byref(t), C.byref(ppt)),
+           "sums_tile_count")
+    return int(t.value), int(ppt.value)
+
+
+def sums_tiles(f: qmc_integrand, r: qmc_rule, i_begin: int, i_end: int, tile_begin: int,
+               tile_end: int, partials, counters=None, stream=None):
+    """qmc_sums_tiles: partials of tiles [tile_begin, tile_end) of [i_begin, i_end)
+    (device tensor of 2 m T doubles, 4 m T complex)."""
+    _check(lib().qmc_sums_tiles(C.byref(f), C.byref(r), int(i_begin), int(i_end), int(tile_begin),
+                                int(tile_end), _ptr(partials), _ptr(counters), _stream(stream)),
+           "sums_tiles")
+    return partials
+
+
+def reduce_tiles(partials, tiles: int, m: int, is_complex: bool, out, stream=None):
+    """qmc_reduce_tiles: the fixed-order fold of tile partials into per-shift sums."""
+    _check(lib().qmc_reduce_tiles(_ptr(partials), int(tiles), int(m), int(bool(is_complex)),
+                                  _ptr(out), _stream(stream)), "reduce_tiles")
     return out
 
 

@@ -168,6 +168,68 @@ int qmc_sums(const qmc_integrand *f, const qmc_rule *rule, uint64_t i_begin, uin
     return QMC_OK;
 }
 
+int qmc_sums_tile_count(uint64_t range_len, uint64_t m, uint64_t *tiles,
+                        uint64_t *points_per_tile) {
+    if (!tiles || !points_per_tile) return QMC_ERR_ARG;
+    if (m < 1 || m > (uint64_t)kMaxShiftGroup) return QMC_ERR_M;
+    const Geometry g = geometry(range_len, (int)m);
+    *tiles = g.tiles;
+    *points_per_tile = (uint64_t)g.spb * g.L;
+    return QMC_OK;
+}
+
+int qmc_sums_tiles(const qmc_integrand *f, const qmc_rule *rule, uint64_t i_begin,
+                   uint64_t i_end, uint64_t tile_begin, uint64_t tile_end, double *partials,
+                   unsigned long long *counters, void *stream) {
+    int st = check_integrand_shape(f);
+    if (st) return st;
+    if ((st = check_rule(rule))) return st;
+    if (f->dim != rule->dim) return QMC_ERR_DIM;
+    if (!partials) return QMC_ERR_ARG;
+    if (rule->m > (uint64_t)kMaxShiftGroup) return QMC_ERR_M;
+    if (i_end <= i_begin || i_end > rule->n) return QMC_ERR_RANGE;
+    const int mg = (int)rule->m;
+    const Geometry g = geometry(i_end - i_begin, mg);
+    if (tile_begin >= tile_end || tile_end > g.tiles) return QMC_ERR_RANGE;
+    if ((st = device_ok())) return st;
+
+    // the tiles of the whole range's decomposition: same L and streams per block, the
+    // first point moved to tile_begin, the global end kept for the ragged last tile
+    SumsParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.n = rule->n;
+    p.i_begin = i_begin + tile_begin * (uint64_t)g.spb * g.L;
+    p.i_end = i_end;
+    p.d = rule->dim;
+    for (int j = 0; j < rule->dim; ++j) p.dc[j] = dim_const(rule->z[j] % rule->n, rule->n);
+    p.t = make_transform(rule->transform);
+    p.fit = rule->fit;
+    fill_integrand(p, f);
+    p.counters = counters;
+    p.m = mg;
+    p.spb = g.spb;
+    p.L = g.L;
+    p.tiles = tile_end - tile_begin;
+    p.shifts = rule->shifts;
+    p.partials = partials;
+    cudaError_t e = launch_sums_any(f->family, p.t.kind, dim3((unsigned)p.tiles), dim3(g.threads),
+                                    (cudaStream_t)stream, p);
+    return e == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+int qmc_reduce_tiles(const double *partials, uint64_t tiles, uint64_t m, int is_complex,
+                     double *sums, void *stream) {
+    if (!partials || !sums || tiles < 1) return QMC_ERR_ARG;
+    if (m < 1 || m > (uint64_t)kMaxShiftGroup) return QMC_ERR_M;
+    int st = device_ok();
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = launch_reduce_tiles(partials, tiles, (int)m, 0, sums, s);
+    if (e == cudaSuccess && is_complex)
+        e = launch_reduce_tiles(partials + 2 * tiles * m, tiles, (int)m, 0, sums + 2 * m, s);
+    return e == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
 int qmc_finalize(const double *sums, uint64_t m, uint64_t n, int is_complex, double *result,
                  double *Q, void *stream) {
     if (!sums || !result) return QMC_ERR_ARG;

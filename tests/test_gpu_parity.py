@@ -203,6 +203,56 @@ def test_ragged_ranges_and_sharding(env):
     assert np.allclose(parts[-2] + parts[-1], Sfull, rtol=1e-15, atol=0)
 
 
+@pytest.mark.parametrize("case", ["real", "complex"])
+def test_tile_sharding_is_bit_identical(env, case):
+    """Shards cut at tile boundaries, their partials assembled in order and folded by
+    qmc_reduce_tiles give qmc_sums bit for bit (the multi-device merge of one rule)."""
+    from paper_1811_11720_gb300 import shard
+    q, torch, dev, tab = env
+    if case == "real":
+        n, d, m, i0 = 108863, 6, 32, 17
+        c, w = W.genz_params(4, d, 3)
+        f = q.Integrand.genz(4, c, w)
+    else:
+        n, d, m, i0 = 4691, 5, 8, 0
+        f = q.Integrand.polynomial(W.feynman_regular(3))
+    cplx = f.is_complex
+    D = _dev_shifts(torch, O.shifts(9, m, d), dev)
+    r = q.rule(n, tab.z_for(n)[:d], D, ("korobov", 3))
+    fd = f.device_struct(dev)
+    ws = torch.empty(q.sums_workspace_bytes(r, cplx, i0, n), dtype=torch.uint8, device=dev)
+    whole = torch.zeros(4 * m, dtype=torch.float64, device=dev)
+    q.sums(fd, r, i0, n, ws, whole)
+    tiles, _ = q.sums_tile_count(n - i0, m)
+    per = 2 * m * (2 if cplx else 1)
+    parts = []
+    for rank in range(3):
+        a, b = shard.shard_tiles(tiles, rank, 3)
+        buf = torch.empty((b - a) * per, dtype=torch.float64, device=dev)
+        q.sums_tiles(fd, r, i0, n, a, b, buf)
+        parts.append(buf.cpu().numpy())
+    allp = torch.from_numpy(shard.assemble_tile_partials(parts, m, cplx)).to(dev)
+    merged = torch.zeros(4 * m, dtype=torch.float64, device=dev)
+    q.reduce_tiles(allp, tiles, m, cplx, merged)
+    torch.cuda.synchronize()
+    k = (4 if cplx else 2) * m
+    assert np.array_equal(merged.cpu().numpy()[:k], whole.cpu().numpy()[:k])
+
+
+def test_tile_sharding_rejects_bad_ranges(env):
+    q, torch, dev, tab = env
+    n, d, m = 4691, 3, 8
+    c, w = W.genz_params(4, d, 3)
+    fd = q.Integrand.genz(4, c, w).device_struct(dev)
+    r = q.rule(n, tab.z_for(n)[:d], _dev_shifts(torch, O.shifts(1, m, d), dev), ("baker",))
+    tiles, _ = q.sums_tile_count(n, m)
+    buf = torch.empty(2 * m * (tiles + 1), dtype=torch.float64, device=dev)
+    for a, b in [(0, 0), (3, 2), (0, tiles + 1)]:
+        with pytest.raises(q.QMCError) as e:
+            q.sums_tiles(fd, r, 0, n, a, b, buf)
+        assert e.value.code == -12
+
+
 def test_deterministic(env):
     q, torch, dev, tab = env
     n, d, m = 108863, 8, 32

@@ -98,3 +98,45 @@ def test_bench_replicas_draw_independent_integrals():
     assert len(a) == len(b) == 45
     assert not any(np.array_equal(x[3], y[3]) for x, y in zip(a, b))
     assert bench.workload_items(0, "4:10:korobov3")[0][:3] == (4, 10, ("korobov", 3))
+
+
+def _tiles_worker(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    import torch
+    import torch.distributed as dist
+    from paper_1811_11720_gb300 import shard
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    tiles, m = 11, 3
+    counts = [shard.shard_tiles(tiles, r, world)[1] - shard.shard_tiles(tiles, r, world)[0]
+              for r in range(world)]
+    a, b = shard.shard_tiles(tiles, rank, world)
+    # synthetic partials: value = tile * 1000 + slot, re block then im block
+    re = np.array([t * 1000.0 + s for t in range(a, b) for s in range(2 * m)])
+    im = -re
+    local = torch.from_numpy(np.concatenate([re, im]))
+    out = shard.gather_tile_partials(local, counts, m, True)
+    np.save(os.path.join(out_dir, f"tiles{rank}.npy"), out)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_tile_partials_assemble_in_tile_order(tmp_path):
+    import torch.multiprocessing as mp
+    world, port = 2, _free_port()
+    mp.start_processes(_tiles_worker, args=(world, port, str(tmp_path)), nprocs=world,
+                       start_method="spawn")
+    m, tiles = 3, 11
+    re = np.array([t * 1000.0 + s for t in range(tiles) for s in range(2 * m)])
+    want = np.concatenate([re, -re])
+    for rank in range(world):
+        assert np.array_equal(np.load(tmp_path / f"tiles{rank}.npy"), want)
+
+
+def test_shard_tiles_cover_exactly():
+    from paper_1811_11720_gb300 import shard
+    for tiles in (1, 5, 4096, 4097):
+        for world in (1, 2, 3, 8):
+            spans = [shard.shard_tiles(tiles, r, world) for r in range(world)]
+            assert spans[0][0] == 0 and spans[-1][1] == tiles
+            assert all(spans[i][1] == spans[i + 1][0] for i in range(world - 1))

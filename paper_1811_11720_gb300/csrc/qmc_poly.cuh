@@ -19,6 +19,7 @@
 #pragma once
 #include <cstdint>
 
+#include "qmc_fp.cuh"
 #include "qmc_params.cuh"
 
 namespace qmc {
@@ -310,10 +311,19 @@ __device__ __forceinline__ double poly_real(const double *x, int nterm, const do
     return s;
 }
 
-// x^y for x > 0 (library pow for non-integer exponents).
+// x^y for x > 0: integer and half-integer |y| <= 16 by repeated squaring and one square
+// root (x^(n + 1/2) = x^n sqrt(x), negative y through one reciprocal), otherwise the
+// library pow.
 __device__ __forceinline__ double pow_pos(double x, double y) {
     if (y == 1.0) return x;
     if (y == -1.0) return 1.0 / x;
+    const double ay = fabs(y), twoy = 2.0 * ay;
+    if (ay <= 16.0 && twoy == floor(twoy) && x > 0.0) {
+        const int n = (int)ay;   // integer part
+        double v = ipow_u(x, n);
+        if (twoy != 2.0 * n) v = n ? v * sqrt(x) : sqrt(x);
+        return y < 0.0 ? 1.0 / v : v;
+    }
     return pow(x, y);
 }
 

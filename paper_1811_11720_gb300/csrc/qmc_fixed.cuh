@@ -3,7 +3,7 @@
 // For Korobov<r,r> the map is phi(v) = v^(r+1) P(v) on v = min(x, 1 - x) in [0, 1/2]
 // (phi(x) = 1 - phi(1 - x) above 1/2), with P(v) = sum_k A_k v^k,
 // A_k = C (-1)^k binom(r,k) / (r+1+k), and the weight is C (v (1 - v))^r.  In w = 1 - v the
-// polynomial has positive integer coefficients, so for r = 1..4 (compiled orders) the map
+// polynomial has positive integer coefficients, so for r = 1..6 (compiled orders) the map
 // is evaluated with unsigned 64-bit integer multiplies, r being a compile-time constant:
 //
 //   * v enters in 0.64 fixed point, V = v 2^64, straight from the top word X of the shifted
@@ -14,10 +14,11 @@
 //     1 + 2w | 1 + 3w + 6w^2 | 1 + 4w + 10w^2 + 20w^3 | 1 + 5w + 15w^2 + 35w^3 + 70w^4.
 //     Unsigned Horner in fixed point with F fractional bits, F the largest value with
 //     P(0) 2^F = sum_k binom(r+k, k) 2^F < 2^64 (every Horner intermediate is at most that
-//     for w <= 1); each step truncates by at most 3 units of 2^-F (F = 62, 60, 58, 57 for
-//     r = 1..4; the products drop their low partial products, see mulhi_trunc).
-//   * phi = v^(r+1) P in 0.64 fixed point; the absolute error is below 2^-54 (the power's
-//     truncations times P <= 126, and the truncations of the last product).  The integrands
+//     for w <= 1); each step truncates by at most 3 units of 2^-F (F = 62, 60, 58, 57, 55,
+//     53 for r = 1..6; the products drop their low partial products, see mulhi_trunc).
+//   * phi = v^(r+1) P in 0.64 fixed point; the absolute error is below 2^-(61 - 1.7 r)
+//     (2^-54.9 for r = 4, 2^-50.9 for r = 6: the power's truncations times
+//     P <= binom(2r+1, r), and the truncations of the last product scaled by 2^(64 - F)).  The integrands
 //     that accept a fixed-point coordinate take it as is; otherwise it is rounded to double.
 //   * t = v (1 - v) = V - V^2 2^-64 in 0.64 fixed point, normalized into the format Fx (a
 //     64-bit mantissa and an exponent) for the running product over the dimensions, whose
@@ -121,6 +122,23 @@ __device__ __forceinline__ double fixed_to_double64(uint64_t x) {
 }
 
 // ---------------------------------------------------------------------------------------
+// v^E 2^64 for V = v 2^64 and V2 = v^2 2^64 (E >= 2): products of squares, E - 1 roundings
+// at most (each truncating by at most 3 units of 2^-64).
+template <int E>
+__device__ __forceinline__ uint64_t fixed_pow(uint64_t V, uint64_t V2) {
+    static_assert(E >= 2, "power");
+    if constexpr (E == 2) {
+        return V2;
+    } else if constexpr (E == 3) {
+        return mulhi_trunc(V2, V);
+    } else {
+        const uint64_t h = fixed_pow<E / 2>(V, V2);
+        const uint64_t sq = mulhi_trunc(h, h);
+        if constexpr (E % 2) return mulhi_trunc(sq, V);
+        else return sq;
+    }
+}
+
 // Horner steps k = K, K-1, ..., 0 of P(w) = sum_k binom(R+k, k) w^k for Korobov<R,R>:
 // p <- floor(p W / 2^64) + binom(R+k, k) 2^F, W = w 2^64.
 template <int R, int K>
@@ -142,26 +160,29 @@ __device__ __forceinline__ uint64_t korobov_phi_fixed(uint64_t V, Fx &Wp) {
     const uint64_t p = korobov_horner<R, R - 1>(top, ~V);
     // v^(r+1) 2^64
     const uint64_t V2 = mulhi_trunc(V, V);
-    uint64_t pw;
-    if constexpr (R == 1) pw = V2;
-    else if constexpr (R == 2) pw = mulhi_trunc(V2, V);
-    else if constexpr (R == 3) pw = mulhi_trunc(V2, V2);
-    else pw = mulhi_trunc(mulhi_trunc(V2, V2), V);
+    const uint64_t pw = fixed_pow<R + 1>(V, V2);
     // t = v - v^2 in 0.64 fixed point (<= 2^62), into the weight product
     Wp = fx_norm(fx_mul(Wp, fx_norm_any(V - V2, 0)));
     return mulhi_trunc(pw, p) << (64 - F);
 }
 
+// Wp^E for a normalized Wp, normalized (binary powering).
+template <int E>
+__device__ __forceinline__ Fx fx_pow(Fx Wp) {
+    if constexpr (E == 1) {
+        return Wp;
+    } else {
+        const Fx h = fx_pow<E / 2>(Wp);
+        const Fx sq = fx_norm(fx_mul(h, h));
+        if constexpr (E % 2) return fx_norm(fx_mul(sq, Wp));
+        else return sq;
+    }
+}
+
 // C^d (prod_j t_j)^r rounded to double; cdx = C^d as Fx.
 template <int R>
 __device__ __forceinline__ double korobov_weight_fixed(Fx Wp, Fx cdx) {
-    Fx w = Wp;
-    if constexpr (R >= 2) {
-        w = fx_norm(fx_mul(Wp, Wp));
-        if constexpr (R == 3) w = fx_mul(w, Wp);
-        else if constexpr (R == 4) w = fx_norm(fx_mul(w, w));
-    }
-    return fx_to_double(fx_mul(w, cdx));
+    return fx_to_double(fx_mul(fx_pow<R>(Wp), cdx));
 }
 
 }  // namespace qmc

@@ -69,7 +69,7 @@ inline TransformParams make_transform(const qmc_transform &t) {
         // binomial expansion of (1-t)^r1 integrated term by term (Eq. (korobov)).
         for (int k = 0; k <= r1; ++k) tp.A[k] = tp.C * ((k & 1) ? -1.0 : 1.0) * binom(r1, k) / (r0 + k + 1);
         for (int k = 0; k <= r0; ++k) tp.B[k] = tp.C * ((k & 1) ? -1.0 : 1.0) * binom(r0, k) / (r1 + k + 1);
-        // Korobov<r,r> with r <= 4 has integer polynomial coefficients and runs on the
+        // Korobov<r,r> with r <= 6 has integer polynomial coefficients (in 1 - u) and runs on the
         // integer pipe (the coefficients are compile-time constants of the kernel)
         if (r0 == r1 && r0 >= 1 && r0 <= kMaxKorobovInt) tp.kind = kTKorobovInt;
     } else if (t.kind == QMC_T_SIDI) {

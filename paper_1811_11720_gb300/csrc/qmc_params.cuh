@@ -15,7 +15,7 @@ constexpr int kSumsThreads = 256;   // threads per block of the lattice-sum kern
 // Internal transform kind: symmetric Korobov<r,r>, 1 <= r <= kMaxKorobovInt, evaluated in
 // integer fixed point (qmc_fixed.cuh).  The public kind stays QMC_T_KOROBOV.
 constexpr int kTKorobovInt = 4;
-constexpr int kMaxKorobovInt = 4;
+constexpr int kMaxKorobovInt = 6;
 
 // Korobov<r0,r1> (Eq. (korobov)) as used by the kernels: for u <= 1/2,
 //   phi(u) = u^(r0+1) sum_k A[k] u^k,  A[k] = C (-1)^k binom(r1,k) / (r0+k+1), k <= r1,

@@ -204,8 +204,16 @@ __device__ __forceinline__ void stream_sums(const P &p, const FamilyShared &fsh,
             stream_sums_r<FAM, TK, 3>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, acc_re, acc_im,
                                       nonfinite, signfail);
             return;
-        default:
+        case 4:
             stream_sums_r<FAM, TK, 4>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, acc_re, acc_im,
+                                      nonfinite, signfail);
+            return;
+        case 5:
+            stream_sums_r<FAM, TK, 5>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, acc_re, acc_im,
+                                      nonfinite, signfail);
+            return;
+        default:
+            stream_sums_r<FAM, TK, 6>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, acc_re, acc_im,
                                       nonfinite, signfail);
             return;
         }

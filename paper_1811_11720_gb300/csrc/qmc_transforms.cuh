@@ -4,7 +4,7 @@
 // FP64 is the scarce unit on GB300, so every step that is exact in integer arithmetic is
 // done on the integer pipe: comparisons of non-negative doubles are integer comparisons
 // of their bit patterns, 1 - u for u >= 1/2 (exact by Sterbenz' lemma) and multiplication
-// by 2 are bit manipulations.  The symmetric Korobov maps r <= 4, baker and the identity
+// by 2 are bit manipulations.  The symmetric Korobov maps r <= 6, baker and the identity
 // also have a fixed-point form (transform_fixed; Korobov in qmc_fixed.cuh) that hands the
 // integrand x in 0.64 fixed point; the FP64 forms here serve the other transforms, the
 // fitted rules and the integrands without a fixed-point form.

@@ -122,10 +122,11 @@ GENZ_CASES = [(fam, d, tr) for fam in (1, 2, 3, 4) for d in (2, 6, 10)
               (2, 4, ("none",)), (5, 5, ("korobov", 3)), (6, 4, ("baker",)),
               (2, 3, ("sidi", 2)), (1, 3, ("sidi", 3)), (4, 5, ("korobov", 2, 5)),
               (2, 16, ("baker",)), (3, 1, ("korobov", 3)),
-              # symmetric r <= 4 runs in integer fixed point; r = 0, r >= 5 and r0 != r1
+              # symmetric r <= 6 runs in integer fixed point; r = 0, r >= 7 and r0 != r1
               # keep the FP64 Horner form
               (1, 10, ("korobov", 4)), (4, 16, ("korobov", 3)), (3, 4, ("korobov", 0)),
-              (4, 6, ("korobov", 5)), (1, 3, ("korobov", 8)), (3, 5, ("korobov", 3, 1)),
+              (4, 6, ("korobov", 5)), (3, 7, ("korobov", 6)), (2, 5, ("korobov", 6)),
+              (1, 3, ("korobov", 8)), (4, 4, ("korobov", 7)), (3, 5, ("korobov", 3, 1)),
               # families 1 and 3-6 take x in fixed point under none, baker and Korobov r <= 4
               (1, 5, ("none",)), (4, 7, ("none",)), (5, 8, ("baker",)), (6, 6, ("korobov", 2)),
               (3, 10, ("baker",)), (4, 12, ("korobov", 1))]
@@ -463,6 +464,28 @@ def test_nonfinite_counted(env):
     D = np.zeros((m, 1), dtype=np.uint64)
     _, _, _, cnt = _gpu_sums(env, f, n, [1], D, ("none",))
     assert cnt[0] == m
+
+
+@pytest.mark.parametrize("n", [2147483647, 2305843009213693951])
+@pytest.mark.parametrize("fam,tr", [(4, ("korobov", 3)), (1, ("korobov", 1)), (3, ("baker",)),
+                                    (4, ("none",))])
+def test_large_n_fixed_point_paths(env, n, fam, tr):
+    """The integer transforms and fixed-point forms on lattices beyond 2^32 points (the
+    GPU-built table's 2^31 - 1, and 2^61 - 1 with a Korobov-type vector z_j = 3^j mod n):
+    sub-ranges at the start, in the middle and at the end against the oracle."""
+    q, torch, dev, tab = env
+    d, m = 6, 8
+    if n in tab:
+        z = [int(v) for v in tab.z_for(n)[:d]]
+    else:
+        z = [pow(3, j, n) for j in range(d)]
+    c, w = W.genz_params(fam, d, 31)
+    D = O.shifts(41, m, d)
+    f = q.Integrand.genz(fam, c, w)
+    for a, b in [(0, 2000), (n // 3, n // 3 + 1500), (n - 1700, n)]:
+        _, gre, _, _ = _gpu_sums(env, f, n, z, D, tr, i0=a, i1=b)
+        o = O.shift_sums(O.genz(fam, c, w), tr, n, z, D, i0=a, i1=b)
+        assert np.all(np.abs((gre[:, 0] + gre[:, 1]) - (o["re"][:, 0] + o["re"][:, 1])) <= TOL * o["abs"])
 
 
 @pytest.mark.parametrize("tr", [("korobov", 3), ("baker",)])

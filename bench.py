@@ -58,7 +58,7 @@ TRAFFIC_BYTES_PER_LAUNCH = 250_880
 
 def fp64_flops_per_eval(family: int, transform, d: int) -> int:
     """Algorithmic FP64 work of one evaluation (add/mul = 1, fma = 2, each library call or
-    division = 1 "special" flop), from the per-family op-count table of the design notes:
+    division = 1 "special" flop), per family and transform:
       Korobov-r: (2r+1) fma for phi, (r+2) mul for w, 1 mul into the product, per dim
       baker: 2 per dim;  oscillatory: d fma + cos;  corner: d fma + ceil(log2(d+1)) mul + div;
       Gaussian: d (sub + fma) + exp;  accumulation: weight multiply + add.
@@ -86,8 +86,8 @@ def fp64_flops_per_eval(family: int, transform, d: int) -> int:
 
 def feynman_flops_per_eval(fl) -> int:
     """Algorithmic FP64 work of one evaluation of the complex deformed integrand U^a F^-b
-    det J (config 3), counted as in the design notes' table (add/mul = 1, fma = 2, each
-    library call = 1): value, gradient and Hessian of F (one fused multiply-add per term and
+    det J (d = 5 Feynman-parameter workload), with the rules of fp64_flops_per_eval
+    (add/mul = 1, fma = 2, each library call = 1): value, gradient and Hessian of F (one fused multiply-add per term and
     derivative, nf (1 + d + d(d+1)/2) of them), U and F at the complex point (a complex
     multiply-add per factor: 8 flops), the deformation and the Jacobian entries (3d + 2d^2),
     complex LU of the d x d Jacobian (8 d^3 / 3), two complex powers (hypot, atan2, log, exp,
@@ -117,7 +117,7 @@ FEYNMAN_INTEGRALS = 4
 def workload_items(rank: int = 0, only: str | None = None, workload: str = "genz"):
     """The 45 (family, d, transform, c, w) Genz integrals, or the single one named by
     ``only`` ("FAMILY:D:TRANSFORM", e.g. "4:10:korobov3") for profiling a small case.
-    workload "feynman" (config 3): four d = 5 complex deformed integrands
+    workload "feynman": four d = 5 complex deformed Feynman-parameter integrands
     (workloads.feynman_regular) with Korobov-3, as (20, 5, transform, FeynmanLike, None)."""
     if workload == "feynman":
         return [(FEYNMAN_FAMILY, 5, ("korobov", 3), W.feynman_regular(1000 + 17 * rank + k), None)
@@ -316,7 +316,7 @@ def run_gpu(args, rank: int, world: int):
 def run_batch_workload(args):
     """Batching (many sector integrals in one launch) against one launch per integral.
 
-    Config-4 shape: `--batch-count` sector integrands U/F^2.5 with positive coefficients,
+    Workload: `--batch-count` sector integrands U/F^2.5 with positive coefficients,
     d ~ U{3..8}, U and F of 10..400 monomials each, m = 32, Korobov-3, the
     variance-reduction fit (histogram + Levenberg-Marquardt) on every second integral, and
     n log-uniform in [1e4, --batch-nmax] snapped to the table.  Every integral is
@@ -426,6 +426,78 @@ def run_batch_workload(args):
 SERVE_EPSABS = 1e-7   # the library's default absolute goal (App. A.1)
 
 
+def run_latency_workload(args):
+    """Latency of one small integral: the d = 4 product peak (c_j = 5, Korobov-3,
+    n = 108863, m = 16; 1.74e6 evaluations per integral) integrated repeatedly.  Three
+    paths: qmc_integrate with host buffers (coefficients and shifts copied in, the result
+    read back: what a caller waits for), the device entry points qmc_sums + qmc_finalize
+    on resident inputs (CUDA events), and the same pair replayed from a CUDA graph.
+    Reports median and 99th-percentile latency per integral in microseconds."""
+    import torch
+
+    import paper_1811_11720_gb300 as q
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    table = q.GenvecTable.load()
+    n, d, m, tr = 108863, 4, 16, ("korobov", 3)
+    c, w = W.product_peak_params(d, args.seed)
+    f = q.Integrand.genz(2, c, w)
+    reps = max(20, args.steps * 40)
+    # host-buffer path
+    for _ in range(5):
+        q.integrate(f, table, n, m, tr, seed=args.seed)
+    torch.cuda.synchronize()
+    host = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        q.integrate(f, table, n, m, tr, seed=args.seed)
+        host.append((time.perf_counter() - t0) * 1e6)
+    # device path on resident inputs
+    D = torch.from_numpy(q.make_shifts(args.seed, m, d).astype(np.int64)).to(dev)
+    r = q.rule(n, table.z_for(n)[:d], D, tr)
+    fd = f.device_struct(dev)
+    ws = torch.empty(q.sums_workspace_bytes(r, False, 0, n), dtype=torch.uint8, device=dev)
+    sums = torch.zeros(4 * m, dtype=torch.float64, device=dev)
+    res = torch.zeros(4, dtype=torch.float64, device=dev)
+    s = torch.cuda.Stream()
+
+    def once():
+        q.sums(fd, r, 0, n, ws, sums, None, s)
+        q.finalize(sums, m, n, False, res, None, s)
+
+    with torch.cuda.stream(s):
+        for _ in range(5):
+            once()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        once()
+    dev_us, graph_us = [], []
+    for lst, fn in ((dev_us, once), (graph_us, g.replay)):
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(s):
+                e0.record(s)
+                fn()
+                e1.record(s)
+            e1.synchronize()
+            lst.append(e0.elapsed_time(e1) * 1e3)
+
+    def pct(v):
+        return {"p50_us": float(np.percentile(v, 50)), "p99_us": float(np.percentile(v, 99))}
+
+    out = {"metric": "product-peak d=4 integral latency", "unit": "us", "higher_is_better": False,
+           "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "product_peak_d4_c5_korobov3_n108863_m16", "repetitions": reps,
+                      "evaluations": n * m},
+           "value": float(np.percentile(host, 50)),
+           "host_buffers": pct(host), "device_entry_points": pct(dev_us),
+           "cuda_graph": pct(graph_us),
+           "device_evals_per_s": n * m / (float(np.percentile(graph_us, 50)) * 1e-6)}
+    print(json.dumps(out))
+
+
 def goal_met(res, epsrel: float, epsabs: float = SERVE_EPSABS) -> bool:
     """The adaptive mode's goal per component (errormode all):
     |error| <= max(epsabs, epsrel |integral|) for the real and the imaginary part."""
@@ -435,7 +507,7 @@ def goal_met(res, epsrel: float, epsabs: float = SERVE_EPSABS) -> bool:
 
 
 def run_serve_workload(args):
-    """Serving: Poisson arrivals of config-3-like integrals (complex, d = 5, contour
+    """Serving: Poisson arrivals of Feynman-parameter-like integrals (complex, d = 5, contour
     deformation with lam = 1, Korobov-3, m = 32; half with F > 0 on the cube, half with F
     changing sign inside), each with a relative error target log-uniform in [1e-8, 1e-3],
     the library's default absolute target 1e-7, and an evaluation budget; continuous batching (qmc_server) against the same arrival
@@ -574,7 +646,8 @@ def main():
     ap.add_argument("--no-kernel-events", dest="kernel_events", action="store_false")
     ap.add_argument("--only", default=None, help="FAMILY:D:TRANSFORM, e.g. 4:10:korobov3")
     ap.add_argument("--n", type=int, default=N_LATTICE, help="lattice size (a table size)")
-    ap.add_argument("--workload", default="genz", choices=["genz", "feynman", "batch", "serve"])
+    ap.add_argument("--workload", default="genz",
+                    choices=["genz", "feynman", "batch", "serve", "latency"])
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--rates", type=float, nargs="*", default=[2.0, 8.0, 32.0])
     ap.add_argument("--serve-maxeval", type=float, default=3.2e7)
@@ -589,6 +662,9 @@ def main():
         return
     if args.workload == "serve":
         run_serve_workload(args)
+        return
+    if args.workload == "latency":
+        run_latency_workload(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -656,7 +732,7 @@ def main():
                 "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2070 MHz",
                 "note": ("achieved counts the method's FP64 flops per evaluation "
                          "(fp64_flops_per_eval); the kernel evaluates the lattice points, "
-                         "Korobov r<=4 and the Genz linear/quadratic forms exactly on the "
+                         "Korobov r<=6 and the Genz linear/quadratic forms exactly on the "
                          "integer pipe, so this FP64-equivalent rate can exceed the FP64 peak")}
     if rank == 0:
         line = dict(base)

@@ -14,7 +14,7 @@
  * (Sec. 2.4, Eq. (ISfit)) and the periodizing transform (Sec. 2.3: Korobov Eq. (korobov),
  * Sidi Eq. (sidi), baker Eq. (baker), or none).
  *
- * Readings taken where the paper leaves a choice (each is also listed in the design notes):
+ * Readings taken where the paper leaves a choice:
  *  - Lattice point.  u = RN( frac(r/n + D 2^-53) ) with r = i z mod n computed exactly and
  *    Delta = D 2^-53 (D a 53-bit integer): the exact rational fractional part rounded
  *    once to the nearest double (ties to even).  u may equal 1.0 when the fraction lies

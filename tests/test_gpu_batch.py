@@ -108,9 +108,9 @@ def test_batch_tuned_shape_matches_oracle(env):
         assert np.all(np.abs(Sg - So) <= 1e-12 * o["abs"]), i
 
 
-def test_sector_batch_config4_shape(env):
-    """Config-4 shape at small n: sector integrands, d 3..8, 10..400 monomials, fit on
-    half, against single launches."""
+def test_sector_batch_workload_shape(env):
+    """The sector batch workload's shape at small n: sector integrands, d 3..8, 10..400
+    monomials, fit on half, against single launches."""
     q, torch, dev, tab = env
     rng = np.random.default_rng(4)
     entries = []

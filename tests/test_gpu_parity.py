@@ -1,8 +1,9 @@
 """GPU parity: the CUDA path through the C ABI against the CPU oracle on identical seeded
 inputs.  Points are compared bit for bit; per-shift sums, the mean and the error within
-1e-12 of the mean |g| (the oracle's double-double sum of |g| / n), the bound derived in
-the design notes from the kernel's FP64 arithmetic (a few ulp per sample, two-level
-summation) with three orders of magnitude of margin."""
+1e-12 of the mean |g| (the oracle's double-double sum of |g| / n): the kernel's arithmetic
+differs from the oracle's by a few ulp per sample (fixed-point forms within ~2^-54
+absolutely) and the two-level summation adds at most ~200 ulp of sum |g|, so ~3e-14 is
+expected and the bound leaves a factor >= 30."""
 import numpy as np
 import pytest
 

@@ -106,7 +106,7 @@ def test_error_estimate_formula():
 
 @pytest.mark.slow
 def test_error_estimate_coverage(genvec_table):
-    """Over many seeds the true value lies within 3 sigma in most cases (config-1 shape,
+    """Over many seeds the true value lies within 3 sigma in most cases (the d = 4 product-peak shape,
     product peak in d = 4, Korobov-3, n = 1021)."""
     n = 1021
     c, w = W.product_peak_params(4, 3)

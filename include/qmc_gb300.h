@@ -195,7 +195,7 @@ int qmc_sums(const qmc_integrand *f, const qmc_rule *rule, uint64_t i_begin, uin
  * per-tile partials live in a fixed device array of QMC_NOALLOC_SCRATCH_BYTES (8 MiB) that
  * every GPU loading the library holds until the process exits.
  *   - Problems whose partials need more than that (qmc_sums_workspace_bytes() >
- *     QMC_NOALLOC_SCRATCH_BYTES, e.g. real m = 32 beyond n ~ 2e9) are rejected with
+ *     QMC_NOALLOC_SCRATCH_BYTES, e.g. real m = 32 beyond n ~ 1.1e9) are rejected with
  *     QMC_ERR_WORKSPACE before anything is launched.
  *   - The first call on a device looks up the array's device address (once per device,
  *     with that device current); make that first call before any stream capture.

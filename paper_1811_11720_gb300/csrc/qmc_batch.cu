@@ -154,7 +154,7 @@ int fill_batch_item(BatchItem &it, const qmc_batch_item &b, int m, int spb, uint
     uint32_t L = Lcfg;
     if (L == 0) {
         Geometry g = geometry(range, m);
-        L = (g.spb == spb) ? g.L : std::max<uint32_t>(32, (uint32_t)std::min<uint64_t>(8192, (range + (uint64_t)spb * kTargetTiles - 1) / ((uint64_t)spb * kTargetTiles)));
+        L = (g.spb == spb) ? g.L : points_per_stream(range, (uint64_t)spb);
     }
     const uint64_t ptile = (uint64_t)spb * L;
     std::memset(&it, 0, sizeof(it));

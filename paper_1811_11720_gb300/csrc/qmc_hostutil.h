@@ -155,15 +155,31 @@ struct Geometry {
 };
 
 constexpr int kMaxShiftGroup = kSumsThreads;   // shifts per launch (block holds spb * m threads)
-constexpr uint64_t kTargetTiles = 4096;
+// Tiles come in whole waves of kWaveTiles blocks (152 SMs x 5 resident blocks of the
+// separable families on GB300): one wave for small ranges, up to kMaxWaves for large ones,
+// so that the last wave is (nearly) full; streams of 8..8192 points.
+constexpr uint64_t kWaveTiles = 152 * 5;
+constexpr uint64_t kMaxWaves = 6;
+constexpr uint64_t kWavePoints = 64;             // points per stream before a new wave
+constexpr uint64_t kMinPointsPerStream = 8;
+constexpr uint64_t kMaxPointsPerStream = 8192;
+
+// Points per stream for a range split over spb streams per tile (a function of the range
+// and spb only, so results do not depend on the device or the grid).
+inline uint32_t points_per_stream(uint64_t range, uint64_t spb) {
+    const uint64_t wave = spb * kWaveTiles * kWavePoints;
+    const uint64_t waves = std::max<uint64_t>(1, std::min<uint64_t>(kMaxWaves, (range + wave - 1) / wave));
+    const uint64_t target = waves * kWaveTiles;
+    uint64_t per = (range + spb * target - 1) / (spb * target);
+    per = std::max<uint64_t>(kMinPointsPerStream, std::min<uint64_t>(kMaxPointsPerStream, per));
+    return (uint32_t)per;
+}
 
 inline Geometry geometry(uint64_t range, int mg) {
     Geometry g;
     g.spb = std::max(1, kSumsThreads / mg);
     g.threads = g.spb * mg;
-    uint64_t per = (range + (uint64_t)g.spb * kTargetTiles - 1) / ((uint64_t)g.spb * kTargetTiles);
-    per = std::max<uint64_t>(32, std::min<uint64_t>(8192, per));
-    g.L = (uint32_t)per;
+    g.L = points_per_stream(range, (uint64_t)g.spb);
     uint64_t ptile = (uint64_t)g.spb * g.L;
     g.tiles = range ? (range + ptile - 1) / ptile : 0;
     return g;

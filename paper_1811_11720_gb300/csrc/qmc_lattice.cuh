@@ -4,7 +4,7 @@
 //     v = frac(r/n + Delta),  r = i z_j mod n,  Delta = D 2^-53  (D a 53-bit integer),
 // and the library's contract is u = RN(v): the exact rational rounded once to the nearest
 // double.  On GB300 the FP64 pipe is the scarce resource (~2 DFMA/clk/SM), while the
-// integer pipe is ~30x wider, so the point never touches FP64:
+// integer pipe is ~30x wider, so the point itself never touches FP64:
 //
 //   * r/n is carried as a 128-bit fixed-point fraction F = floor(r 2^128 / n) plus the
 //     exact remainder rem = r 2^128 mod n.  Stepping i -> i+1 adds the constants
@@ -16,8 +16,9 @@
 //     or rem != 0).  When V's high word is zero (v < 2^-64, which needs r/n + Delta within
 //     2^-64 of an integer) more quotient bits are produced from rem by long division.
 //
-// Everything here is exact integer arithmetic; the only floating-point object is the final
-// bit pattern.
+// Everything here is exact integer arithmetic; the only floating-point objects are the
+// final bit pattern and, at the start of a stream, FP64 estimates of a quotient that is
+// then corrected exactly (divmod_128_64_fast).
 #pragma once
 #include <cstdint>
 
@@ -47,6 +48,43 @@ __host__ __device__ inline void divmod_128_64(uint64_t hi, uint64_t lo, uint64_t
     *r = hi;
 }
 
+// The same quotient and remainder for n < 2^62 in a few dozen instructions: a quotient
+// estimate q0 from FP64 (within 2^13 + 2 of the exact one: the operands and 1/n carry
+// relative errors of a few 2^-53), the exact remainder r = p - q0 n in two's-complement
+// 128-bit arithmetic (|r| < 2^14 n), a second FP64 estimate of r / n (within 1), and at
+// most two exact corrections.  The result is exact; only the work differs from the loop.
+__device__ __forceinline__ void divmod_128_64_fast(uint64_t hi, uint64_t lo, uint64_t n,
+                                                   uint64_t *q, uint64_t *r) {
+    if (n >= (1ull << 62)) {
+        divmod_128_64(hi, lo, n, q, r);
+        return;
+    }
+    const double inv = 1.0 / (double)n;
+    const double pd = fma((double)hi, 0x1p64, (double)lo);
+    const double qd = fmin(fmax(pd * inv, 0.0), 0x1.fffffffffffffp63);
+    const uint64_t q0 = (uint64_t)qd;
+    const uint64_t ml = q0 * n, mh = __umul64hi(q0, n);
+    const uint64_t rl = lo - ml;
+    const uint64_t rh = hi - mh - (lo < ml ? 1ull : 0ull);   // r = (int64)rh 2^64 + rl
+    const double rd = fma((double)(long long)rh, 0x1p64, (double)rl);
+    const long long q1 = (long long)floor(rd * inv);
+    // r - q1 n lies in (-2n, 2n), inside the int64 range for n < 2^62: its low word is it
+    long long r2 = (long long)(rl - (uint64_t)q1 * n);
+    uint64_t qq = q0 + (uint64_t)q1;
+#pragma unroll 1
+    for (int it = 0; it < 3 && r2 < 0; ++it) {
+        r2 += (long long)n;
+        --qq;
+    }
+#pragma unroll 1
+    for (int it = 0; it < 3 && r2 >= (long long)n; ++it) {
+        r2 -= (long long)n;
+        ++qq;
+    }
+    *q = qq;
+    *r = (uint64_t)r2;
+}
+
 // Lattice state of one coordinate at index i: F(i) and rem(i) for r = i z mod n.
 // F(i) = (i Fz + floor(i remz / n)) mod 2^128, rem(i) = i remz mod n.
 __device__ __forceinline__ void lattice_state_at(uint64_t i, const DimConst &c, uint64_t n,
@@ -55,7 +93,7 @@ __device__ __forceinline__ void lattice_state_at(uint64_t i, const DimConst &c, 
     uint64_t p_lo = i * c.remz;
     uint64_t p_hi = __umul64hi(i, c.remz);  // i < n and remz < n: p < n^2, p_hi < n
     uint64_t q;
-    divmod_128_64(p_hi, p_lo, n, &q, &rem);
+    divmod_128_64_fast(p_hi, p_lo, n, &q, &rem);
     uint64_t lo = i * c.fz_lo;
     uint64_t hi = __umul64hi(i, c.fz_lo) + i * c.fz_hi;
     f_lo = lo + q;

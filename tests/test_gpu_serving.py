@@ -71,9 +71,12 @@ def test_server_matches_adaptive_integrate(env):
 
 def test_memory_budget_limits_concurrency(env):
     q, torch, tab = env
-    # each request reserves ~0.45 MB (complex partials of its largest lattice, n = 108863,
-    # plus coefficients and shifts) and the fixed buffers take ~20 KB: two fit in 1 MB
-    srv = q.Server(tab, memory_budget=1_000_000, max_slots=8, m=32)
+    # each request reserves the complex partials of its largest lattice (n = 108863: tiles x
+    # 32 shifts x 4 doubles) plus a few KB of coefficients and shifts; the fixed buffers
+    # take ~20 KB: a budget of 2.5 requests' partials fits two, not three
+    tiles, _ = q.sums_tile_count(108863, 32)
+    per_request = tiles * 32 * 4 * 8
+    srv = q.Server(tab, memory_budget=int(2.5 * per_request) + 64 * 1024, max_slots=8, m=32)
     ids = [srv.submit(_feyn(q, 40 + i), epsrel=1e-2, maxeval=4_000_000, seed=i) for i in range(6)]
     most = 0
     for _ in range(300):

@@ -18,10 +18,10 @@ template <int FAM, int TK>
 __device__ __forceinline__ void batch_stream(const BatchItem &it, const FamilyShared &fsh,
                                              const double *s_fit, const uint64_t *dsh,
                                              uint64_t i0, uint64_t cnt, WarpLattice *wl,
-                                             double &acc_re, double &acc_im,
+                                             int q, double &acc_re, double &acc_im,
                                              unsigned long long &nonfinite,
                                              unsigned long long &signfail) {
-    stream_sums<FAM, TK>(it, fsh, s_fit, it.fit != nullptr, dsh, it.cd, i0, cnt, wl, acc_re,
+    stream_sums<FAM, TK>(it, fsh, s_fit, it.fit != nullptr, dsh, it.cd, i0, cnt, wl, q, acc_re,
                          acc_im, nonfinite, signfail);
 }
 
@@ -75,22 +75,23 @@ __global__ void __launch_bounds__(kSumsThreads)
         if (active && i0 < it.i_end) cnt = (it.i_end - i0 < it.L) ? (it.i_end - i0) : it.L;
         double acc_re = 0.0, acc_im = 0.0;
         unsigned long long nonfinite = 0, signfail = 0;
-        WarpLattice *wl = (m & 31) ? nullptr : &s_lat[tid >> 5];
+        const int qlanes = lattice_group_lanes(m, d);
+        WarpLattice *wl = qlanes ? &s_lat[tid >> 5] : nullptr;
         switch (it.t.kind) {
         case QMC_T_NONE:
-            batch_stream<FAM, QMC_T_NONE>(it, fsh, s_fit, dsh, i0, cnt, wl, acc_re, acc_im, nonfinite, signfail);
+            batch_stream<FAM, QMC_T_NONE>(it, fsh, s_fit, dsh, i0, cnt, wl, qlanes, acc_re, acc_im, nonfinite, signfail);
             break;
         case QMC_T_BAKER:
-            batch_stream<FAM, QMC_T_BAKER>(it, fsh, s_fit, dsh, i0, cnt, wl, acc_re, acc_im, nonfinite, signfail);
+            batch_stream<FAM, QMC_T_BAKER>(it, fsh, s_fit, dsh, i0, cnt, wl, qlanes, acc_re, acc_im, nonfinite, signfail);
             break;
         case QMC_T_KOROBOV:
-            batch_stream<FAM, QMC_T_KOROBOV>(it, fsh, s_fit, dsh, i0, cnt, wl, acc_re, acc_im, nonfinite, signfail);
+            batch_stream<FAM, QMC_T_KOROBOV>(it, fsh, s_fit, dsh, i0, cnt, wl, qlanes, acc_re, acc_im, nonfinite, signfail);
             break;
         case kTKorobovInt:
-            batch_stream<FAM, kTKorobovInt>(it, fsh, s_fit, dsh, i0, cnt, wl, acc_re, acc_im, nonfinite, signfail);
+            batch_stream<FAM, kTKorobovInt>(it, fsh, s_fit, dsh, i0, cnt, wl, qlanes, acc_re, acc_im, nonfinite, signfail);
             break;
         default:
-            batch_stream<FAM, QMC_T_SIDI>(it, fsh, s_fit, dsh, i0, cnt, wl, acc_re, acc_im, nonfinite, signfail);
+            batch_stream<FAM, QMC_T_SIDI>(it, fsh, s_fit, dsh, i0, cnt, wl, qlanes, acc_re, acc_im, nonfinite, signfail);
             break;
         }
         double *base = partials + it.partial_off;

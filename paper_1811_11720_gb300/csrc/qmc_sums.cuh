@@ -54,13 +54,22 @@ __device__ __forceinline__ void prepare_fit(const double *fit, int d, double *s_
     }
 }
 
-// Per-warp lattice state for the warp-cooperative path: two buffers of d coordinates each
-// (the state at point t is written to buffer t & 1), in shared memory.
+// Per-warp lattice state for the shared-state path: two buffers (the state at point t is
+// written to buffer t & 1) of one slot per lane, in shared memory.
 struct WarpLattice {
-    uint64_t fhi[2][kMaxDim];
-    uint64_t flo[2][kMaxDim];
-    uint64_t rem[2][kMaxDim];
+    uint64_t fhi[2][32];
+    uint64_t flo[2][32];
+    uint64_t rem[2][32];
 };
+
+// Lanes per stream group of a warp for the shared-state path: 32 when m is a multiple of
+// 32, m when m divides 32 and the stream's shifts can hold the d coordinates; 0 otherwise
+// (each thread keeps its own state).
+__device__ __forceinline__ int lattice_group_lanes(int m, int d) {
+    if (m % 32 == 0) return 32;
+    if (32 % m == 0 && d <= m) return m;
+    return 0;
+}
 
 // One evaluation of g at the point whose coordinate j has lattice state (fhi(j), flo(j),
 // rem(j)); adds it to the two-level accumulator.
@@ -107,17 +116,19 @@ __device__ __forceinline__ void eval_point(const P &p, const FamilyShared &fsh, 
 // P (fields n, d, dc[], t).  Two-level FP64 accumulation: blocks of kInner samples, then
 // the block sums (rounding error ~ (kInner + L/kInner) ulp instead of L ulp).
 //
-// Lattice state.  When a warp's 32 lanes are 32 shifts of the same stream (m a multiple of
-// 32; wl != nullptr), the state is shared: lane j < d keeps coordinate j in registers,
-// computes its start point and steps it, and publishes it to the warp's shared buffer once
-// per point; every lane reads the d coordinates from there (broadcast loads).  That is one
-// lattice step per lane and point instead of d.  Otherwise each thread keeps all d
-// coordinates in local memory (L1) and steps them itself.
+// Lattice state.  When the q = lattice_group_lanes(m, d) lanes of a warp group are q shifts
+// of the same stream (wl != nullptr; q = 32 for m a multiple of 32, q = m for m = 2..16
+// with d <= m), the state is shared: the group's lane j < d keeps coordinate j in
+// registers, computes its start point and steps it, and publishes it to the warp's shared
+// buffer once per point; every lane of the group reads the d coordinates from there
+// (broadcast loads), with one __syncwarp over the group per point.  That is one lattice
+// step per lane and point instead of d.  Otherwise each thread keeps all d coordinates in
+// local memory (L1) and steps them itself.
 template <int FAM, int TK, int R, class P>
 __device__ __forceinline__ void stream_sums_r(const P &p, const FamilyShared &fsh, const double *s_fit,
                                               bool use_fit, const uint64_t *dsh, double cd,
                                               uint64_t i0, uint64_t cnt, WarpLattice *wl,
-                                              double &acc_re, double &acc_im,
+                                              int q, double &acc_re, double &acc_im,
                                               unsigned long long &nonfinite,
                                               unsigned long long &signfail) {
     constexpr bool kCplx = FamilyAcc<FAM>::kComplex;
@@ -140,7 +151,8 @@ __device__ __forceinline__ void stream_sums_r(const P &p, const FamilyShared &fs
             }
         }
     };
-    if (wl) {
+    if (wl && q == 32) {
+        // the warp is one group: lane j < d owns coordinate j
         const int lane = threadIdx.x & 31;
         uint64_t fh = 0, fl = 0, rm = 0;
         if (lane < d) lattice_state_at(i0, p.dc[lane], n, fh, fl, rm);
@@ -162,6 +174,33 @@ __device__ __forceinline__ void stream_sums_r(const P &p, const FamilyShared &fs
                 g_im, signfail);
             accumulate(t, g_re, g_im);
             if (lane < d) lattice_step(p.dc[lane], n, fh, fl, rm);
+        }
+    } else if (wl) {
+        // groups of q < 32 lanes (q divides 32): the group's lane j < d owns coordinate j
+        const int lane = threadIdx.x & 31;
+        const int base = lane & ~(q - 1);
+        const int pos = lane - base;
+        const unsigned mask = ((1u << q) - 1u) << base;
+        uint64_t fh = 0, fl = 0, rm = 0;
+        if (pos < d) lattice_state_at(i0, p.dc[pos], n, fh, fl, rm);
+#pragma unroll 1
+        for (uint64_t t = 0; t < cnt; ++t) {
+            const int b = (int)(t & 1);
+            if (pos < d) {
+                wl->fhi[b][lane] = fh;
+                if constexpr (TK != kTKorobovInt) {
+                    wl->flo[b][lane] = fl;
+                    wl->rem[b][lane] = rm;
+                }
+            }
+            __syncwarp(mask);
+            double g_re, g_im = 0.0;
+            eval_point<FAM, TK, R>(
+                p, fsh, s_fit, use_fit, dsh, cd, [&](int j) { return wl->fhi[b][base + j]; },
+                [&](int j) { return wl->flo[b][base + j]; },
+                [&](int j) { return wl->rem[b][base + j]; }, g_re, g_im, signfail);
+            accumulate(t, g_re, g_im);
+            if (pos < d) lattice_step(p.dc[pos], n, fh, fl, rm);
         }
     } else {
         uint64_t fhi[kMaxDim], flo[kMaxDim], rem[kMaxDim];
@@ -186,39 +225,39 @@ __device__ __forceinline__ void stream_sums_r(const P &p, const FamilyShared &fs
 template <int FAM, int TK, class P>
 __device__ __forceinline__ void stream_sums(const P &p, const FamilyShared &fsh, const double *s_fit,
                                             bool use_fit, const uint64_t *dsh, double cd,
-                                            uint64_t i0, uint64_t cnt, WarpLattice *wl,
+                                            uint64_t i0, uint64_t cnt, WarpLattice *wl, int q,
                                             double &acc_re, double &acc_im,
                                             unsigned long long &nonfinite,
                                             unsigned long long &signfail) {
     if constexpr (TK == kTKorobovInt) {
         switch (p.t.r0) {
         case 1:
-            stream_sums_r<FAM, TK, 1>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, acc_re, acc_im,
+            stream_sums_r<FAM, TK, 1>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, q, acc_re, acc_im,
                                       nonfinite, signfail);
             return;
         case 2:
-            stream_sums_r<FAM, TK, 2>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, acc_re, acc_im,
+            stream_sums_r<FAM, TK, 2>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, q, acc_re, acc_im,
                                       nonfinite, signfail);
             return;
         case 3:
-            stream_sums_r<FAM, TK, 3>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, acc_re, acc_im,
+            stream_sums_r<FAM, TK, 3>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, q, acc_re, acc_im,
                                       nonfinite, signfail);
             return;
         case 4:
-            stream_sums_r<FAM, TK, 4>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, acc_re, acc_im,
+            stream_sums_r<FAM, TK, 4>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, q, acc_re, acc_im,
                                       nonfinite, signfail);
             return;
         case 5:
-            stream_sums_r<FAM, TK, 5>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, acc_re, acc_im,
+            stream_sums_r<FAM, TK, 5>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, q, acc_re, acc_im,
                                       nonfinite, signfail);
             return;
         default:
-            stream_sums_r<FAM, TK, 6>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, acc_re, acc_im,
+            stream_sums_r<FAM, TK, 6>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, q, acc_re, acc_im,
                                       nonfinite, signfail);
             return;
         }
     } else {
-        stream_sums_r<FAM, TK, 0>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, acc_re, acc_im,
+        stream_sums_r<FAM, TK, 0>(p, fsh, s_fit, use_fit, dsh, cd, i0, cnt, wl, q, acc_re, acc_im,
                                   nonfinite, signfail);
     }
 }
@@ -289,8 +328,9 @@ __global__ void __launch_bounds__(kSumsThreads, kSumsMinBlocks<FAM>)
         uint64_t cnt = 0;
         if (active && i0 < p.i_end) cnt = (p.i_end - i0 < p.L) ? (p.i_end - i0) : p.L;
         double acc_re, acc_im;
+        const int q = lattice_group_lanes(m, d);
         stream_sums<FAM, TK>(p, fsh, s_fit, p.fit != nullptr, dsh, cd, i0, cnt,
-                             (m & 31) ? nullptr : &s_lat[tid >> 5], acc_re, acc_im, nonfinite,
+                             q ? &s_lat[tid >> 5] : nullptr, q, acc_re, acc_im, nonfinite,
                              signfail);
         double *out_re = p.partials + 2 * (tile * (uint64_t)m);
         double *out_im = p.partials + 2 * (p.tiles * (uint64_t)m) + 2 * (tile * (uint64_t)m);

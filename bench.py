@@ -51,9 +51,9 @@ SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) of one lattice-sum launch from the ncu capture of the current
 # kernel (profiles/sums_kernel_gauss_d10_korobov3_n1072187_m32.md: Gaussian, d = 10,
 # Korobov-3, n = 1,072,187).  The kernel reads kilobytes of constants and writes the tile
-# partials, whose number does not grow with n (about 4096 tiles), so the figure applies
-# to the benchmark's launches as measured.  None once the kernel changes.
-TRAFFIC_BYTES_PER_LAUNCH = 250_880
+# partials, whose number does not grow with n (whole waves of 760 tiles, at most six), so
+# the figure applies to the benchmark's launches as measured.  None once the kernel changes.
+TRAFFIC_BYTES_PER_LAUNCH = 274_432
 
 
 def fp64_flops_per_eval(family: int, transform, d: int) -> int:

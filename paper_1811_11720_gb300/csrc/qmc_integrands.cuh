@@ -24,19 +24,24 @@
 
 namespace qmc {
 
-// Fixed-point constants of the separable Genz families 1 and 3-6, whose linear and
-// quadratic forms run on the integer pipe when the coordinate arrives in 0.64 fixed point:
+// Fixed-point constants of the separable Genz families 1-6, whose linear and quadratic
+// forms run on the integer pipe when the coordinate arrives in 0.64 fixed point:
 //   linear (1, 3, 5, 6): cl_j = c_j 2^S with S = 62 - floor(log2 sum_j c_j), so every
 //     partial sum of c_j x_j (or c_j |x_j - w_j|) stays below 2^63;
-//   Gaussian (4): cq_j = c_j 2^S with S = 61 - floor(log2 max_j c_j), so |c_j (x_j - w_j)|
-//     2^S < 2^62 and each square (2^(2S - 64) scale) is below 2^60.
+//   Gaussian (4) and product peak (2): cq_j = c_j 2^S with S = 61 - floor(log2 max_j c_j),
+//     so |c_j (x_j - w_j)| 2^S < 2^62 and each square (2^(2S - 64) scale) is below 2^60.
+//     A square keeps only 2S - 64 fractional bits, so these forms need S >= 57 (max c < 32,
+//     at least 50 fractional bits); the product peak also caps S at 62, so that 1 at the
+//     square's scale, one = 2^(2S - 64), is at most 2^60 and 1 + q_j^2 fits below 2^61.
 // Each term truncates by at most three units (2^-S, or 2^(64 - 2S) for squares); the forms
-// are therefore exact to ~2^-56 absolutely for the benchmark's c (||c||_1 <= 18).  ok is
-// false (double path) unless every c_j >= 0 and 0 <= w_j <= 1.
+// are therefore exact to ~2^-48 absolutely or better.  ok is false (double path) unless
+// every c_j >= 0 and 0 <= w_j <= 1.
 struct FixedForms {
     uint64_t cl[kMaxDim];
     uint64_t cq[kMaxDim];
     uint64_t w64[kMaxDim];   // w_j 2^64, at most 2^64 - 1
+    uint64_t one;            // 2^(2S - 64) (product peak)
+    double num;              // prod_j c_j^2 (product peak)
     int S;
     bool ok;
 };
@@ -56,9 +61,9 @@ struct FamilyShared {
 };
 
 template <int FAM>
-constexpr bool kHasFixedForm = FAM == QMC_GENZ_OSCILLATORY || FAM == QMC_GENZ_CORNER_PEAK ||
-                               FAM == QMC_GENZ_GAUSSIAN || FAM == QMC_GENZ_C0 ||
-                               FAM == QMC_GENZ_DISCONTINUOUS;
+constexpr bool kHasFixedForm = FAM == QMC_GENZ_OSCILLATORY || FAM == QMC_GENZ_PRODUCT_PEAK ||
+                               FAM == QMC_GENZ_CORNER_PEAK || FAM == QMC_GENZ_GAUSSIAN ||
+                               FAM == QMC_GENZ_C0 || FAM == QMC_GENZ_DISCONTINUOUS;
 
 // v 2^-S for an integer v < 2^64, rounded once (the power of two is exact; v 2^-S is normal).
 __device__ __forceinline__ double scaled_fixed(uint64_t v, int S) {
@@ -82,8 +87,15 @@ __device__ __forceinline__ void stage_fixed_forms(const P &p, FixedForms &fx) {
         cmax = fmax(cmax, c);
     }
     int S;
-    if constexpr (FAM == QMC_GENZ_GAUSSIAN) S = cmax > 0.0 ? 61 - ilogb(cmax) : 61;
-    else S = csum > 0.0 ? 62 - ilogb(csum) : 62;
+    if constexpr (FAM == QMC_GENZ_GAUSSIAN) {
+        S = cmax > 0.0 ? 61 - ilogb(cmax) : 61;
+        ok = ok && S >= 57;
+    } else if constexpr (FAM == QMC_GENZ_PRODUCT_PEAK) {
+        S = cmax > 0.0 ? min(61 - ilogb(cmax), 62) : 62;
+        ok = ok && S >= 57;
+    } else {
+        S = csum > 0.0 ? 62 - ilogb(csum) : 62;
+    }
     ok = ok && S >= 1 && S <= 120;
     if (ok) {
         const double c = p.c[tid];
@@ -93,6 +105,12 @@ __device__ __forceinline__ void stage_fixed_forms(const P &p, FixedForms &fx) {
         fx.w64[tid] = w >= 1.0 ? 0xFFFFFFFFFFFFFFFFull : __double2ull_rz(ldexp(w, 64));
     }
     if (tid == 0) {
+        if constexpr (FAM == QMC_GENZ_PRODUCT_PEAK) {
+            double num = 1.0;
+            for (int i = 0; ok && i < p.d; ++i) num *= p.c[i] * p.c[i];
+            fx.num = num;
+            fx.one = ok ? 1ull << (2 * S - 64) : 0ull;
+        }
         fx.S = S;
         fx.ok = ok;
     }
@@ -192,6 +210,22 @@ struct FamilyAcc<QMC_GENZ_PRODUCT_PEAK> {
     __device__ __forceinline__ void finish(int, const FamilyShared &, double &re, double &im,
                                            unsigned long long &) {
         re = 1.0 / prod;
+        im = 0.0;
+    }
+    // fixed point: f = prod c_j^2 / prod (1 + q_j^2), q_j = c_j |x_j - w_j|; each factor
+    // 1 + q_j^2 at scale 2^(2S - 64) (below 2^61, at least 2^50), the product in Fx
+    Fx pf;
+    __device__ __forceinline__ void init_fixed() { pf = {0x8000000000000000ull, 1}; }
+    __device__ __forceinline__ void add_fixed(int j, uint64_t x, const FamilyShared &fs) {
+        const uint64_t w = fs.fx.w64[j];
+        const uint64_t a = x >= w ? x - w : w - x;                       // |x - w| 2^64
+        const uint64_t q = mulhi_trunc(a, fs.fx.cq[j]);                 // c |x - w| 2^S
+        const uint64_t s = fs.fx.one + mulhi_trunc(q, q);               // (1 + q^2) 2^(2S-64)
+        pf = fx_norm(fx_mul(pf, fx_norm({s, 128 - 2 * fs.fx.S})));
+    }
+    __device__ __forceinline__ void finish_fixed(int, const FamilyShared &fs, double &re,
+                                                 double &im, unsigned long long &) {
+        re = fs.fx.num / fx_to_double(pf);
         im = 0.0;
     }
 };

@@ -130,7 +130,9 @@ GENZ_CASES = [(fam, d, tr) for fam in (1, 2, 3, 4) for d in (2, 6, 10)
               (1, 3, ("korobov", 8)), (4, 4, ("korobov", 7)), (3, 5, ("korobov", 3, 1)),
               # families 1 and 3-6 take x in fixed point under none, baker and Korobov r <= 4
               (1, 5, ("none",)), (4, 7, ("none",)), (5, 8, ("baker",)), (6, 6, ("korobov", 2)),
-              (3, 10, ("baker",)), (4, 12, ("korobov", 1))]
+              (3, 10, ("baker",)), (4, 12, ("korobov", 1)),
+              # family 2 takes x in fixed point too (product of 1 + q^2 in Fx)
+              (2, 8, ("korobov", 1)), (2, 12, ("korobov", 2)), (2, 7, ("korobov", 4))]
 
 
 @pytest.mark.parametrize("fam,d,tr", GENZ_CASES)
@@ -151,7 +153,7 @@ def test_genz_sums_match_oracle(env, fam, d, tr):
     assert cnt[0] == 0
 
 
-@pytest.mark.parametrize("fam", [1, 3, 4, 5, 6])
+@pytest.mark.parametrize("fam", [1, 2, 3, 4, 5, 6])
 def test_genz_outside_fixed_point_range(env, fam):
     """Parameters outside the Genz ranges (a negative c_j, w_j > 1) take the FP64 form of
     the integrand; results still match the oracle."""
@@ -165,6 +167,30 @@ def test_genz_outside_fixed_point_range(env, fam):
         res, gre, _, cnt = _gpu_sums(env, q.Integrand.genz(fam, c, w), n, z, D, tr)
         o = O.shift_sums(O.genz(fam, c, w), tr, n, z, D)
         _compare(gre, None, o, n)
+
+
+@pytest.mark.parametrize("fam", [2, 4])
+@pytest.mark.parametrize("c", [[1e3, 3.0, 0.5], [0.01, 0.002, 0.03], [31.0, 1.0, 2.0],
+                               [32.0, 1.0, 2.0], [0.0, 2.0, 1.0]])
+def test_quadratic_form_scale_limits(env, fam, c):
+    """Product peak and Gaussian at the limits of their fixed-point scale: max c = 1000 and
+    32 (S < 57, FP64 form), max c = 31 (S = 57, the widest fixed-point case), small c (the
+    product peak caps S at 62) and a zero c_j.  Both factors have relative condition number
+    up to ~c in the coordinate, so an absolute coordinate difference of 1e-17 between the
+    two Korobov forms already moves f by c 1e-17 relatively (c = 2e4 missed the 1e-12
+    tolerance by that alone): c stays at 1000 or below."""
+    q, torch, dev, tab = env
+    n, m = 4691, 8
+    c = np.array(c)
+    w = np.array([0.3, 0.85, 0.6])
+    d = len(c)
+    z = tab.z_for(n)[:d]
+    D = O.shifts(91 + fam + int(c[0]), m, d)
+    for tr in (("korobov", 3), ("baker",)):
+        res, gre, _, cnt = _gpu_sums(env, q.Integrand.genz(fam, c, w), n, z, D, tr)
+        o = O.shift_sums(O.genz(fam, c, w), tr, n, z, D)
+        _compare(gre, None, o, n)
+        assert cnt[0] == 0
 
 
 def test_config1_product_peak_full_size(env):

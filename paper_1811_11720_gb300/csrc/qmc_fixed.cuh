@@ -20,11 +20,13 @@
 //     (2^-54.9 for r = 4, 2^-50.9 for r = 6: the power's truncations times
 //     P <= binom(2r+1, r), and the truncations of the last product scaled by 2^(64 - F)).  The integrands
 //     that accept a fixed-point coordinate take it as is; otherwise it is rounded to double.
-//   * t = v (1 - v) = V - V^2 2^-64 in 0.64 fixed point, normalized into the format Fx (a
-//     64-bit mantissa and an exponent) for the running product over the dimensions, whose
-//     r-th power times C^d is rounded once to double: the product keeps relative precision
-//     however small it becomes, and each t is exact to 3 2^-64 absolutely, which moves the
-//     weight by less than 2^-58 of its largest value C^d 4^(-rd).
+//   * t = v (1 - v) = V - V^2 2^-64 in 0.64 fixed point enters the running product over
+//     the dimensions, kept in the format Fx (a 64-bit mantissa, renormalized after each
+//     factor, and an exponent), whose r-th power times C^d is rounded once to double: the
+//     product keeps relative precision however small it becomes.  Each t is exact to
+//     3 2^-64 absolutely, which moves the weight by less than 2^-58 of its largest value
+//     C^d 4^(-rd); t itself is not normalized (its low bits are all it has), so a factor
+//     t >= 2^-k costs the product about 2^-(62-k) relatively.
 //
 // GB300 runs ~2 FP64 fused multiply-adds per clock per SM but ~32x as many 32-bit integer
 // multiply-adds, so the ~8 FP64 instructions per dimension of the FP64 form cost more than
@@ -104,7 +106,7 @@ __device__ __forceinline__ Fx fx_norm_any(uint64_t m, int e) {
 // Round to the nearest double (ties to even on the truncated mantissa).  Zero, and values
 // below the normal range, give 0.
 __device__ __forceinline__ double fx_to_double(Fx a) {
-    a = fx_norm(a);
+    a = fx_norm_any(a.m, a.e);
     const int be = a.e + 1021;   // biased exponent minus one
     if (!a.m || be < 0) return 0.0;
     uint64_t mant = a.m >> 11;
@@ -112,6 +114,18 @@ __device__ __forceinline__ double fx_to_double(Fx a) {
     const uint64_t sticky = a.m & 0x3FFull;
     mant += rb & ((sticky != 0) | (mant & 1u));
     // adding the mantissa with its leading one to (exponent - 1) << 52 carries correctly
+    return __longlong_as_double((long long)(((uint64_t)be << 52) + mant));
+}
+
+// The same for a normalized (or zero) mantissa, with overflow to +infinity.
+__device__ __forceinline__ double fx_to_double_sat(Fx a) {
+    const int be = a.e + 1021;
+    if (!a.m || be < 0) return 0.0;
+    if (be > 2045) return __longlong_as_double(0x7FF0000000000000ll);
+    uint64_t mant = a.m >> 11;
+    const uint64_t rb = (a.m >> 10) & 1u;
+    const uint64_t sticky = a.m & 0x3FFull;
+    mant += rb & ((sticky != 0) | (mant & 1u));
     return __longlong_as_double((long long)(((uint64_t)be << 52) + mant));
 }
 
@@ -161,8 +175,10 @@ __device__ __forceinline__ uint64_t korobov_phi_fixed(uint64_t V, Fx &Wp) {
     // v^(r+1) 2^64
     const uint64_t V2 = mulhi_trunc(V, V);
     const uint64_t pw = fixed_pow<R + 1>(V, V2);
-    // t = v - v^2 in 0.64 fixed point (<= 2^62), into the weight product
-    Wp = fx_norm(fx_mul(Wp, fx_norm_any(V - V2, 0)));
+    // t = v - v^2 in 0.64 fixed point (<= 2^62), into the weight product as it is: its
+    // leading zeros carry no information (t is exact to 3 2^-64 absolutely), and the
+    // product, at least 2^31 for t >= 2^-32, is renormalized afterwards
+    Wp = fx_norm(fx_mul(Wp, Fx{V - V2, 0}));
     return mulhi_trunc(pw, p) << (64 - F);
 }
 

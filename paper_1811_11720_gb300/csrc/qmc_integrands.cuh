@@ -33,6 +33,8 @@ namespace qmc {
 //     A square keeps only 2S - 64 fractional bits, so these forms need S >= 57 (max c < 32,
 //     at least 50 fractional bits); the product peak also caps S at 62, so that 1 at the
 //     square's scale, one = 2^(2S - 64), is at most 2^60 and 1 + q_j^2 fits below 2^61.
+// S is capped at 64 otherwise (small c keep 2^-64 absolute precision), so that the
+// exponential's argument scale, S or 2S - 64, lies in [2, 64] (exp_fixed).
 // Each term truncates by at most three units (2^-S, or 2^(64 - 2S) for squares); the forms
 // are therefore exact to ~2^-48 absolutely or better.  ok is false (double path) unless
 // every c_j >= 0 and 0 <= w_j <= 1.
@@ -55,7 +57,7 @@ struct FamilyShared {
     double sub_hi[256];     // the same for j = 8 + bit
     double s0;
     int64_t h[kMaxDim];
-    double exp2t[32];       // 2^(j/32) for exp_table (families with an exponential)
+    uint64_t exp2q[64];     // 2^(j/64) 2^63 for exp_fixed (families with an exponential)
     FixedForms fx;
     PolyShared poly;
 };
@@ -88,15 +90,15 @@ __device__ __forceinline__ void stage_fixed_forms(const P &p, FixedForms &fx) {
     }
     int S;
     if constexpr (FAM == QMC_GENZ_GAUSSIAN) {
-        S = cmax > 0.0 ? 61 - ilogb(cmax) : 61;
+        S = cmax > 0.0 ? min(61 - ilogb(cmax), 64) : 64;
         ok = ok && S >= 57;
     } else if constexpr (FAM == QMC_GENZ_PRODUCT_PEAK) {
         S = cmax > 0.0 ? min(61 - ilogb(cmax), 62) : 62;
         ok = ok && S >= 57;
     } else {
-        S = csum > 0.0 ? 62 - ilogb(csum) : 62;
+        S = csum > 0.0 ? min(62 - ilogb(csum), 64) : 64;
     }
-    ok = ok && S >= 1 && S <= 120;
+    ok = ok && S >= 2;
     if (ok) {
         const double c = p.c[tid];
         const double w = p.w ? p.w[tid] : 0.0;
@@ -152,7 +154,7 @@ __device__ __forceinline__ void stage_family(const P &p, FamilyShared &fs) {
         if constexpr (kHasFixedForm<FAM>) stage_fixed_forms<FAM>(p, fs.fx);
         if constexpr (FAM == QMC_GENZ_GAUSSIAN || FAM == QMC_GENZ_C0 ||
                       FAM == QMC_GENZ_DISCONTINUOUS) {
-            if (tid < 32) fs.exp2t[tid] = kExp2Table[tid];
+            for (int i = tid; i < 64; i += blockDim.x) fs.exp2q[i] = kExp2Fixed[i];
         }
     }
 }
@@ -286,7 +288,7 @@ struct FamilyAcc<QMC_GENZ_GAUSSIAN> {
     }
     __device__ __forceinline__ void finish_fixed(int, const FamilyShared &fs, double &re,
                                                  double &im, unsigned long long &) {
-        re = exp_table(-scaled_fixed(sq, 2 * fs.fx.S - 64), fs.exp2t);
+        re = fx_to_double_sat(exp_fixed(sq, 2 * fs.fx.S - 64, true, fs.exp2q));
         im = 0.0;
     }
 };
@@ -315,7 +317,7 @@ struct FamilyAcc<QMC_GENZ_C0> {
     }
     __device__ __forceinline__ void finish_fixed(int, const FamilyShared &fs, double &re,
                                                  double &im, unsigned long long &) {
-        re = exp_table(-scaled_fixed(sl, fs.fx.S), fs.exp2t);
+        re = fx_to_double_sat(exp_fixed(sl, fs.fx.S, true, fs.exp2q));
         im = 0.0;
     }
 };
@@ -348,7 +350,7 @@ struct FamilyAcc<QMC_GENZ_DISCONTINUOUS> {
     }
     __device__ __forceinline__ void finish_fixed(int, const FamilyShared &fs, double &re,
                                                  double &im, unsigned long long &) {
-        re = zero ? 0.0 : exp_table(scaled_fixed(sl, fs.fx.S), fs.exp2t);
+        re = zero ? 0.0 : fx_to_double_sat(exp_fixed(sl, fs.fx.S, false, fs.exp2q));
         im = 0.0;
     }
 };

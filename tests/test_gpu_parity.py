@@ -169,6 +169,28 @@ def test_genz_outside_fixed_point_range(env, fam):
         _compare(gre, None, o, n)
 
 
+@pytest.mark.parametrize("fam,c", [(5, [300.0, 2.0, 1.0]), (6, [300.0, 2.0, 1.0]),
+                                   (4, [1e-3, 2e-3, 5e-4]), (5, [1e-3, 2e-3, 5e-4]),
+                                   (6, [1e-3, 2e-3, 5e-4]), (4, [31.0, 0.0, 20.0]),
+                                   (5, [0.0, 0.0, 0.0])])
+def test_exponential_forms_range(env, fam, c):
+    """The integer exponential over its argument range: e^(+-303) (exponent scale 2^54),
+    tiny c (scale capped at 2^64, the largest shift), the widest Gaussian and a zero
+    argument, under the fixed-point transforms."""
+    q, torch, dev, tab = env
+    n, m = 4691, 8
+    c = np.array(c)
+    w = np.array([0.3, 0.85, 0.6])
+    d = len(c)
+    z = tab.z_for(n)[:d]
+    D = O.shifts(57 + fam, m, d)
+    for tr in (("korobov", 3), ("baker",), ("none",)):
+        res, gre, _, cnt = _gpu_sums(env, q.Integrand.genz(fam, c, w), n, z, D, tr)
+        o = O.shift_sums(O.genz(fam, c, w), tr, n, z, D)
+        _compare(gre, None, o, n)
+        assert cnt[0] == 0
+
+
 @pytest.mark.parametrize("fam", [2, 4])
 @pytest.mark.parametrize("c", [[1e3, 3.0, 0.5], [0.01, 0.002, 0.03], [31.0, 1.0, 2.0],
                                [32.0, 1.0, 2.0], [0.0, 2.0, 1.0]])

@@ -1,9 +1,9 @@
-// qmc_exp.cuh -- e^(+-a) on the integer pipe for the separable Genz integrands, whose
-// exponent arrives as a fixed-point sum A 2^-E (the Gaussian, C0 and discontinuous forms).
-// The method is P. T. P. Tang's table-driven exponential ("Table-driven implementation of
-// the exponential function in IEEE floating-point arithmetic", ACM TOMS 15 (1989)
-// 144-157), carried out in 64-bit fixed point instead of FP64:
+// qmc_exp.cuh -- e^x for the separable Genz integrands by the table-driven method of
+// P. T. P. Tang ("Table-driven implementation of the exponential function in IEEE
+// floating-point arithmetic", ACM TOMS 15 (1989) 144-157), in two forms.
 //
+// exp_fixed: e^(+-a) for a fixed-point argument a = A 2^-E (the Gaussian, C0 and
+// discontinuous forms), carried out in 64-bit integer arithmetic:
 //   * u = a log2(e) = A L 2^-(E + 63) with L = log2(e) 2^63 rounded: the 128-bit product
 //     holds u exactly up to L's rounding (relative 2^-64); its integer part k and its
 //     fraction F = frac(u) 2^64 are two shifts of the product's words by E - 1 bits.
@@ -15,11 +15,27 @@
 //     on Y = y 2^70 with coefficients 2^(-6 (k - 1))/k! 2^64, and the product
 //     2^(j/64) (1 + (e^y - 1)) lands in [2^63, 2^64): a normalized mantissa.
 //   Every product is a truncated high word (mulhi_trunc); the result is within 2^-55
-//   relative of e^(+-a) before its single rounding to double (exhaustive random checks
-//   in exact arithmetic give 0.15 units of 2^-53).
+//   relative of e^(+-a) before its single rounding to double (random checks in exact
+//   arithmetic give at most 0.15 units of 2^-53).
+//
+// exp_table: the same method in FP64 for a double argument x = (32 m + j) ln2/32 + r,
+// |r| <= ln2/64, so e^x = 2^m 2^(j/32) e^r:
+//   * k = 32 m + j = round(x 32/ln2) by adding 1.5 2^52 (the rounded k lands in the low
+//     mantissa bits); r = x - k ln2/32 by two fused multiply-adds with ln2/32 split into
+//     L1 = RN(ln2/32) and L2 = RN(ln2/32 - L1);
+//   * e^r - 1 = r + r^2 (1/2 + r/6 + r^2/24 + r^3/120 + r^4/720) (Taylor; the omitted
+//     r^7/5040 is below 2^-58 relative for |r| <= ln2/64);
+//   * 2^(j/32) from a 32-entry table (the even entries of the fixed-point table rounded to
+//     double, which are the correctly rounded values), the product t (1 + p) as one fused
+//     multiply-add, and 2^m added to the exponent field on the integer pipe.
+//   Ten FP64 instructions, within about 1 ulp; arguments outside [-708.3, 709] (where 2^m
+//   would leave the normal range) take the library exp.
 //
 // GB300 issues ~2 FP64 fused multiply-adds per clock per SM against ~32x as many integer
-// multiply-adds; the ~60 integer instructions here replace ~13 FP64 instructions.
+// multiply-adds.  The integer form (~60 integer instructions for ~13 FP64 ones) pays when
+// the rest of the evaluation leaves the integer pipes idle (baker, Korobov r <= 2); under
+// the integer Korobov r >= 3 the integer pipes are the bottleneck and the FP64 form, on the
+// otherwise idle FP64 pipe, is faster.
 #pragma once
 #include <cstdint>
 
@@ -78,6 +94,33 @@ __device__ __forceinline__ Fx exp_fixed(uint64_t A, int E, bool negate, const ui
     const uint64_t em1 = Y + mulhi_trunc(Y, mulhi_trunc(Y, G));     // (e^y - 1) 2^70
     const uint64_t t = tab[F >> 58];
     return Fx{t + (mulhi_trunc(t, em1) >> 6), ke + 1};
+}
+
+// tab: 2^(j/32), j = 0..31, staged in shared memory (exp2_table_entry).
+__device__ __forceinline__ double exp_table(double x, const double *tab) {
+    if (!(x >= -708.3 && x <= 709.0)) return exp(x);   // also NaN
+    const double kInvL = 0x1.71547652b82fep+5;        // 32 / ln2
+    const double kL1 = 0x1.62e42fefa39efp-6;          // ln2 / 32, rounded
+    const double kL2 = 0x1.abc9e3b39803fp-61;         // ln2 / 32 - kL1, rounded
+    const double kShift = 0x1.8p52;
+    const double t = fma(x, kInvL, kShift);
+    const int k = (int)(uint32_t)__double_as_longlong(t);   // low word: round(x 32/ln2)
+    const double kd = t - kShift;
+    double r = fma(kd, -kL1, x);
+    r = fma(kd, -kL2, r);
+    double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
+    q = fma(q, r, 1.0 / 24.0);
+    q = fma(q, r, 1.0 / 6.0);
+    q = fma(q, r, 0.5);
+    const double p = fma(r * r, q, r);
+    const double tj = tab[k & 31];
+    const double v = fma(tj, p, tj);
+    return __longlong_as_double(__double_as_longlong(v) + ((long long)(k >> 5) << 52));
+}
+
+// 2^(j/32) as the correctly rounded double: entry 2j of kExp2Fixed rounded to 53 bits.
+__device__ __forceinline__ double exp2_table_entry(int j) {
+    return __ull2double_rn(kExp2Fixed[2 * j]) * 0x1p-63;
 }
 
 }  // namespace qmc

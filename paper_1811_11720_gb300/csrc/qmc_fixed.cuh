@@ -129,6 +129,50 @@ __device__ __forceinline__ double fx_to_double_sat(Fx a) {
     return __longlong_as_double((long long)(((uint64_t)be << 52) + mant));
 }
 
+// a^p for a normalized a and a runtime p >= 1 (binary powering from the top bit; the loop
+// is uniform when p is).  Each product truncates by at most 2^-61 relatively.
+__device__ __forceinline__ Fx fx_powi(Fx a, int p) {
+    Fx r = a;
+#pragma unroll 1
+    for (int i = 30 - __clz(p); i >= 0; --i) {
+        r = fx_norm(fx_mul(r, r));
+        if ((p >> i) & 1) r = fx_norm(fx_mul(r, a));
+    }
+    return r;
+}
+
+// 1/a for a normalized a = m 2^(e - 64): R = 2^127 / m (R < 2^64 for m > 2^63) by Newton's
+// iteration R <- R + R (2^127 - m R) 2^-127 from a single-precision seed (rcp.approx of
+// the top 32 bits, relative error ~2^-22), two steps (2^-44, then below 2^-61: at most 4
+// units low).  m within 2^32 of 2^63 takes the first-order value 2^64 - 2 (m - 2^63)
+// (exact to 4 units there), m = 2^63 the exact power of two.  The result may fall a few
+// units below 2^63; fx_to_double renormalizes.
+__device__ __forceinline__ Fx fx_recip(Fx a) {
+    const uint64_t m = a.m;
+    const uint32_t mh = (uint32_t)(m >> 32);
+    if (mh == 0x80000000u) {
+        const uint64_t dl = m - 0x8000000000000000ull;
+        if (!dl) return Fx{0x8000000000000000ull, 2 - a.e};
+        return Fx{0 - 2 * dl, 1 - a.e};
+    }
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(__uint2float_rn(mh)));
+    const uint32_t rb = __float_as_uint(r);                 // r = 2^E (1 + f), E = -32 or -31
+    const int E = (int)(rb >> 23) - 127;
+    const uint64_t mant = (uint64_t)((rb & 0x7FFFFFu) | 0x800000u);
+    uint64_t R = E >= -31 ? 0xFFFFFFFFFFFFFFFFull : mant << (72 + E);   // r 2^95
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const uint64_t plo = m * R, phi = __umul64hi(m, R);
+        // high word of 2^127 - m R (two's complement; |2^127 - m R| < 2^107)
+        const uint64_t ehi = 0x8000000000000000ull - phi - (plo != 0 ? 1ull : 0ull);
+        const bool neg = (long long)ehi < 0;
+        const uint64_t c = __umul64hi(R, neg ? 0 - ehi : ehi) << 1;
+        R = neg ? R - c : R + c;
+    }
+    return Fx{R, 1 - a.e};
+}
+
 // x 2^-64 for a 0.64 fixed-point x, rounded to nearest.
 __device__ __forceinline__ double fixed_to_double64(uint64_t x) {
     const long long b = __double_as_longlong(__ull2double_rn(x));

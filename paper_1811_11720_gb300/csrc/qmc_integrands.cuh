@@ -16,6 +16,7 @@
 #pragma once
 #include <cstdint>
 
+#include "qmc_cos.cuh"
 #include "qmc_exp.cuh"
 #include "qmc_fp.cuh"
 #include "qmc_params.cuh"
@@ -38,10 +39,17 @@ namespace qmc {
 // Each term truncates by at most three units (2^-S, or 2^(64 - 2S) for squares); the forms
 // are therefore exact to ~2^-48 absolutely or better.  ok is false (double path) unless
 // every c_j >= 0 and 0 <= w_j <= 1.
+//   oscillatory (1), integer finish: the phase in turns, (w_1 + sum_j c_j x_j / (2 pi)) mod 1
+//     as a 64-bit fraction: c_j / (2 pi) = tk_j + tg_j 2^-64 (integer and fraction parts,
+//     from a double-double product), so each term is tk_j X_j + floor(tg_j X_j 2^-64) mod
+//     2^64 and the wrap of the 64-bit sum is the reduction mod 1.
 struct FixedForms {
     uint64_t cl[kMaxDim];
     uint64_t cq[kMaxDim];
     uint64_t w64[kMaxDim];   // w_j 2^64, at most 2^64 - 1
+    uint64_t tk[kMaxDim];    // oscillatory: integer part of c_j / (2 pi)
+    uint64_t tg[kMaxDim];    // oscillatory: fraction of c_j / (2 pi), 2^64 scale
+    uint64_t t0;             // oscillatory: w_1 2^64 mod 2^64
     uint64_t one;            // 2^(2S - 64) (product peak)
     double num;              // prod_j c_j^2 (product peak)
     int S;
@@ -57,7 +65,11 @@ struct FamilyShared {
     double sub_hi[256];     // the same for j = 8 + bit
     double s0;
     int64_t h[kMaxDim];
-    uint64_t exp2q[64];     // 2^(j/64) 2^63 for exp_fixed (families with an exponential)
+    union {
+        uint64_t exp2q[64];     // 2^(j/64) 2^63 for exp_fixed (families with an exponential)
+        uint64_t cos256[65];    // cos(2 pi i/256) 2^62 for cos_turns_fixed (oscillatory)
+    };
+    double exp2t[32];       // 2^(j/32) for exp_table
     FixedForms fx;
     PolyShared poly;
 };
@@ -84,7 +96,7 @@ __device__ __forceinline__ void stage_fixed_forms(const P &p, FixedForms &fx) {
     for (int i = 0; ok && i < p.d; ++i) {
         const double c = p.c[i];
         const double w = p.w ? p.w[i] : 0.0;
-        ok = c >= 0.0 && w >= 0.0 && w <= 1.0;
+        ok = c >= 0.0 && w >= 0.0 && w <= 1.0 && (FAM != QMC_GENZ_OSCILLATORY || c < 0x1p40);
         csum += c;
         cmax = fmax(cmax, c);
     }
@@ -105,8 +117,28 @@ __device__ __forceinline__ void stage_fixed_forms(const P &p, FixedForms &fx) {
         fx.cl[tid] = __double2ull_rz(ldexp(c, S));
         fx.cq[tid] = __double2ull_rz(ldexp(c, S));
         fx.w64[tid] = w >= 1.0 ? 0xFFFFFFFFFFFFFFFFull : __double2ull_rz(ldexp(w, 64));
+        if constexpr (FAM == QMC_GENZ_OSCILLATORY) {
+            // c / (2 pi) = hi + lo (double-double), then integer part and 64-bit fraction
+            constexpr double kInv2PiHi = 0x1.45f306dc9c883p-3;
+            constexpr double kInv2PiLo = -0x1.6b01ec5417056p-57;
+            const double hi = c * kInv2PiHi;
+            const double lo = fma(c, kInv2PiHi, -hi) + c * kInv2PiLo;
+            double k = floor(hi);
+            const double f = hi - k;                                  // exact, in [0, 1)
+            long long g_lo = llrint(ldexp(lo, 64));                   // |lo| 2^64 < 2^12 hi
+            uint64_t g = __double2ull_rz(ldexp(f, 64)) + (uint64_t)g_lo;
+            // a carry out of (or borrow into) the fraction moves the integer part
+            if (g_lo < 0 && g > __double2ull_rz(ldexp(f, 64))) k -= 1.0;
+            if (g_lo > 0 && g < __double2ull_rz(ldexp(f, 64))) k += 1.0;
+            fx.tg[tid] = g;
+            fx.tk[tid] = (uint64_t)(long long)k;
+        }
     }
     if (tid == 0) {
+        if constexpr (FAM == QMC_GENZ_OSCILLATORY) {
+            const double w1 = p.w ? p.w[0] : 0.0;
+            fx.t0 = ok ? (w1 >= 1.0 ? 0ull : __double2ull_rz(ldexp(w1, 64))) : 0ull;
+        }
         if constexpr (FAM == QMC_GENZ_PRODUCT_PEAK) {
             double num = 1.0;
             for (int i = 0; ok && i < p.d; ++i) num *= p.c[i] * p.c[i];
@@ -152,9 +184,13 @@ __device__ __forceinline__ void stage_family(const P &p, FamilyShared &fs) {
             }
         }
         if constexpr (kHasFixedForm<FAM>) stage_fixed_forms<FAM>(p, fs.fx);
+        if constexpr (FAM == QMC_GENZ_OSCILLATORY) {
+            for (int i = tid; i < 65; i += blockDim.x) fs.cos256[i] = kCos256[i];
+        }
         if constexpr (FAM == QMC_GENZ_GAUSSIAN || FAM == QMC_GENZ_C0 ||
                       FAM == QMC_GENZ_DISCONTINUOUS) {
             for (int i = tid; i < 64; i += blockDim.x) fs.exp2q[i] = kExp2Fixed[i];
+            for (int i = tid; i < 32; i += blockDim.x) fs.exp2t[i] = exp2_table_entry(i);
         }
     }
 }
@@ -185,15 +221,20 @@ struct FamilyAcc<QMC_GENZ_OSCILLATORY> {
         re = cos(mask ? s + reflected_c_sum(mask, d, fs) : s);
         im = 0.0;
     }
-    // fixed point: sum c_j x_j on the integer pipe
+    // fixed point: sum c_j x_j on the integer pipe, either scaled by 2^S (then cos in FP64)
+    // or, for the integer finish, as the phase in turns mod 1 (FixedForms)
     uint64_t sl;
     __device__ __forceinline__ void init_fixed() { sl = 0; }
+    template <bool kInt>
     __device__ __forceinline__ void add_fixed(int j, uint64_t x, const FamilyShared &fs) {
-        sl += mulhi_trunc(x, fs.fx.cl[j]);
+        if constexpr (kInt) sl += x * fs.fx.tk[j] + mulhi_trunc(x, fs.fx.tg[j]);
+        else sl += mulhi_trunc(x, fs.fx.cl[j]);
     }
+    template <bool kInt>
     __device__ __forceinline__ void finish_fixed(int, const FamilyShared &fs, double &re,
                                                  double &im, unsigned long long &) {
-        re = cos(fs.s0 + scaled_fixed(sl, fs.fx.S));
+        if constexpr (kInt) re = cos_turns_fixed(sl + fs.fx.t0, fs.cos256);
+        else re = cos(fs.s0 + scaled_fixed(sl, fs.fx.S));
         im = 0.0;
     }
 };
@@ -218,6 +259,7 @@ struct FamilyAcc<QMC_GENZ_PRODUCT_PEAK> {
     // 1 + q_j^2 at scale 2^(2S - 64) (below 2^61, at least 2^50), the product in Fx
     Fx pf;
     __device__ __forceinline__ void init_fixed() { pf = {0x8000000000000000ull, 1}; }
+    template <bool kInt>
     __device__ __forceinline__ void add_fixed(int j, uint64_t x, const FamilyShared &fs) {
         const uint64_t w = fs.fx.w64[j];
         const uint64_t a = x >= w ? x - w : w - x;                       // |x - w| 2^64
@@ -225,6 +267,7 @@ struct FamilyAcc<QMC_GENZ_PRODUCT_PEAK> {
         const uint64_t s = fs.fx.one + mulhi_trunc(q, q);               // (1 + q^2) 2^(2S-64)
         pf = fx_norm(fx_mul(pf, fx_norm({s, 128 - 2 * fs.fx.S})));
     }
+    template <bool kInt>
     __device__ __forceinline__ void finish_fixed(int, const FamilyShared &fs, double &re,
                                                  double &im, unsigned long long &) {
         re = fs.fx.num / fx_to_double(pf);
@@ -251,12 +294,23 @@ struct FamilyAcc<QMC_GENZ_CORNER_PEAK> {
     }
     uint64_t sl;
     __device__ __forceinline__ void init_fixed() { sl = 0; }
+    template <bool kInt>
     __device__ __forceinline__ void add_fixed(int j, uint64_t x, const FamilyShared &fs) {
         sl += mulhi_trunc(x, fs.fx.cl[j]);
     }
+    template <bool kInt>
     __device__ __forceinline__ void finish_fixed(int d, const FamilyShared &fs, double &re,
                                                  double &im, unsigned long long &) {
-        re = 1.0 / ipow_u(1.0 + scaled_fixed(sl, fs.fx.S), d + 1);
+        if constexpr (kInt) {
+            // 1 + s as Fx (s = sl 2^-S, sl < 2^63; S = 64 drops sl's lowest bit), its
+            // (d+1)-th power and the reciprocal, all on the integer pipe
+            const int S = fs.fx.S;
+            const Fx b = S <= 63 ? fx_norm_any((1ull << S) + sl, 64 - S)
+                                 : Fx{0x8000000000000000ull + (sl >> 1), 1};
+            re = fx_to_double(fx_recip(fx_powi(b, d + 1)));
+        } else {
+            re = 1.0 / ipow_u(1.0 + scaled_fixed(sl, fs.fx.S), d + 1);
+        }
         im = 0.0;
     }
 };
@@ -280,15 +334,18 @@ struct FamilyAcc<QMC_GENZ_GAUSSIAN> {
     // fixed point: q = c |x - w| 2^S < 2^62, q^2 2^(2S - 64) < 2^60, summed in 64 bits
     uint64_t sq;
     __device__ __forceinline__ void init_fixed() { sq = 0; }
+    template <bool kInt>
     __device__ __forceinline__ void add_fixed(int j, uint64_t x, const FamilyShared &fs) {
         const uint64_t w = fs.fx.w64[j];
         const uint64_t a = x >= w ? x - w : w - x;                       // |x - w| 2^64
         const uint64_t q = mulhi_trunc(a, fs.fx.cq[j]);                 // c |x - w| 2^S
         sq += mulhi_trunc(q, q);
     }
+    template <bool kInt>
     __device__ __forceinline__ void finish_fixed(int, const FamilyShared &fs, double &re,
                                                  double &im, unsigned long long &) {
-        re = fx_to_double_sat(exp_fixed(sq, 2 * fs.fx.S - 64, true, fs.exp2q));
+        if constexpr (kInt) re = fx_to_double_sat(exp_fixed(sq, 2 * fs.fx.S - 64, true, fs.exp2q));
+        else re = exp_table(-scaled_fixed(sq, 2 * fs.fx.S - 64), fs.exp2t);
         im = 0.0;
     }
 };
@@ -310,14 +367,17 @@ struct FamilyAcc<QMC_GENZ_C0> {
     }
     uint64_t sl;
     __device__ __forceinline__ void init_fixed() { sl = 0; }
+    template <bool kInt>
     __device__ __forceinline__ void add_fixed(int j, uint64_t x, const FamilyShared &fs) {
         const uint64_t w = fs.fx.w64[j];
         const uint64_t a = x >= w ? x - w : w - x;                       // |x - w| 2^64
         sl += mulhi_trunc(a, fs.fx.cl[j]);
     }
+    template <bool kInt>
     __device__ __forceinline__ void finish_fixed(int, const FamilyShared &fs, double &re,
                                                  double &im, unsigned long long &) {
-        re = fx_to_double_sat(exp_fixed(sl, fs.fx.S, true, fs.exp2q));
+        if constexpr (kInt) re = fx_to_double_sat(exp_fixed(sl, fs.fx.S, true, fs.exp2q));
+        else re = exp_table(-scaled_fixed(sl, fs.fx.S), fs.exp2t);
         im = 0.0;
     }
 };
@@ -344,13 +404,16 @@ struct FamilyAcc<QMC_GENZ_DISCONTINUOUS> {
     }
     uint64_t sl;
     __device__ __forceinline__ void init_fixed() { sl = 0; zero = false; }
+    template <bool kInt>
     __device__ __forceinline__ void add_fixed(int j, uint64_t x, const FamilyShared &fs) {
         if (j < 2) zero |= x > fs.fx.w64[j];
         sl += mulhi_trunc(x, fs.fx.cl[j]);
     }
+    template <bool kInt>
     __device__ __forceinline__ void finish_fixed(int, const FamilyShared &fs, double &re,
                                                  double &im, unsigned long long &) {
-        re = zero ? 0.0 : fx_to_double_sat(exp_fixed(sl, fs.fx.S, false, fs.exp2q));
+        if constexpr (kInt) re = zero ? 0.0 : fx_to_double_sat(exp_fixed(sl, fs.fx.S, false, fs.exp2q));
+        else re = zero ? 0.0 : exp_table(scaled_fixed(sl, fs.fx.S), fs.exp2t);
         im = 0.0;
     }
 };

@@ -84,11 +84,16 @@ __device__ __forceinline__ void eval_point(const P &p, const FamilyShared &fsh, 
         // coordinate and integrand form entirely in fixed point (no fit: the fit map
         // needs x as a double)
         if (!use_fit && fsh.fx.ok) {
+            // the final function (exp, power, cos) on the integer pipe where the map leaves
+            // it idle; under Korobov r >= 3 the integer pipes are the bottleneck and the
+            // FP64 form is faster
+            constexpr bool kIntFinish = TK != kTKorobovInt || R <= 2;
             fa.init_fixed();
 #pragma unroll 1
-            for (int j = 0; j < p.d; ++j) fa.add_fixed(j, transform_fixed<TK, R>(fhi(j) + dsh[j], W), fsh);
+            for (int j = 0; j < p.d; ++j)
+                fa.template add_fixed<kIntFinish>(j, transform_fixed<TK, R>(fhi(j) + dsh[j], W), fsh);
             const double wt = weight_finish<TK, R>(W, p.t, cd);
-            fa.finish_fixed(p.d, fsh, g_re, g_im, signfail);
+            fa.template finish_fixed<kIntFinish>(p.d, fsh, g_re, g_im, signfail);
             g_re *= wt;
             return;
         }

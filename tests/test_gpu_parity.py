@@ -132,7 +132,10 @@ GENZ_CASES = [(fam, d, tr) for fam in (1, 2, 3, 4) for d in (2, 6, 10)
               (1, 5, ("none",)), (4, 7, ("none",)), (5, 8, ("baker",)), (6, 6, ("korobov", 2)),
               (3, 10, ("baker",)), (4, 12, ("korobov", 1)),
               # family 2 takes x in fixed point too (product of 1 + q^2 in Fx)
-              (2, 8, ("korobov", 1)), (2, 12, ("korobov", 2)), (2, 7, ("korobov", 4))]
+              (2, 8, ("korobov", 1)), (2, 12, ("korobov", 2)), (2, 7, ("korobov", 4)),
+              # integer finishes (exp, power and reciprocal) under baker, none, Korobov r <= 2
+              (3, 9, ("korobov", 2)), (3, 16, ("korobov", 1)), (3, 3, ("none",)),
+              (4, 9, ("korobov", 2)), (5, 11, ("korobov", 1)), (6, 9, ("none",))]
 
 
 @pytest.mark.parametrize("fam,d,tr", GENZ_CASES)
@@ -187,6 +190,50 @@ def test_exponential_forms_range(env, fam, c):
     for tr in (("korobov", 3), ("baker",), ("none",)):
         res, gre, _, cnt = _gpu_sums(env, q.Integrand.genz(fam, c, w), n, z, D, tr)
         o = O.shift_sums(O.genz(fam, c, w), tr, n, z, D)
+        _compare(gre, None, o, n)
+        assert cnt[0] == 0
+
+
+@pytest.mark.parametrize("c,w1", [([20.0, 7.0, 13.0], 0.3), ([1e-3, 2e-3, 5e-4], 0.999),
+                                  ([0.0, 0.0, 0.0], 0.2), ([6.283185307179586, 3.0, 0.5], 1.0),
+                                  ([1000.0, 1.0, 2.0], 0.0)])
+def test_oscillatory_turns_range(env, c, w1):
+    """Oscillatory cos(2 pi w_1 + sum c_j x_j) with the phase in turns and the integer cos:
+    c_j above 2 pi (integer turns per unit x), tiny c, c = 0 (f = cos(2 pi w_1) constant),
+    c_1 = 2 pi and w_1 = 1, and c_1 = 1000 (condition number 1000 in the coordinate), under
+    baker, none and Korobov-1/2.  (c = 0 with w_1 = 1/4 is left out: there f is 0 exactly
+    in turns but 6.1e-17 through the rounded FP64 argument of the oracle's cos.)"""
+    q, torch, dev, tab = env
+    n, m = 4691, 8
+    c = np.array(c)
+    d = len(c)
+    w = np.array([w1, 0.5, 0.5])
+    z = tab.z_for(n)[:d]
+    D = O.shifts(13 + int(c[0]), m, d)
+    for tr in (("baker",), ("none",), ("korobov", 1), ("korobov", 2)):
+        res, gre, _, cnt = _gpu_sums(env, q.Integrand.genz(1, c, w), n, z, D, tr)
+        o = O.shift_sums(O.genz(1, c, w), tr, n, z, D)
+        _compare(gre, None, o, n)
+        assert cnt[0] == 0
+
+
+@pytest.mark.parametrize("c", [[500.0, 300.0, 200.0], [1e-3, 2e-3, 5e-4], [0.0, 0.0, 0.0],
+                               [1.0, 0.5, 0.25, 0.125, 2.0, 3.0, 0.75, 1.5, 0.1, 0.2, 0.3,
+                                0.4, 0.5, 0.6, 0.7, 0.8]])
+def test_corner_peak_power_range(env, c):
+    """Corner peak (1 + s)^-(d+1) with the integer power and reciprocal: a large s (the
+    result near 1e-11), tiny c (scale capped at 2^64, s below 2^-9), c = 0 (f = 1) and
+    d = 16 (the 17th power), under baker, none and Korobov-1/2."""
+    q, torch, dev, tab = env
+    n, m = 4691, 8
+    c = np.array(c)
+    d = len(c)
+    w = np.full(d, 0.5)
+    z = tab.z_for(n)[:d] if d <= 10 else L.cbc_naive(n, d)[0]
+    D = O.shifts(31 + d, m, d)
+    for tr in (("baker",), ("none",), ("korobov", 1), ("korobov", 2)):
+        res, gre, _, cnt = _gpu_sums(env, q.Integrand.genz(3, c, w), n, z, D, tr)
+        o = O.shift_sums(O.genz(3, c, w), tr, n, z, D)
         _compare(gre, None, o, n)
         assert cnt[0] == 0
 

@@ -85,9 +85,10 @@ __device__ __forceinline__ void eval_point(const P &p, const FamilyShared &fsh, 
         // needs x as a double)
         if (!use_fit && fsh.fx.ok) {
             // the final function (exp, power, cos) on the integer pipe where the map leaves
-            // it idle; under Korobov r >= 3 the integer pipes are the bottleneck and the
-            // FP64 form is faster
-            constexpr bool kIntFinish = TK != kTKorobovInt || R <= 2;
+            // it room; under the higher Korobov orders the integer multiply pipe is the
+            // bottleneck and the FP64 form, on the otherwise idle FP64 pipe, is faster (the
+            // crossover order per family was measured)
+            constexpr bool kIntFinish = TK != kTKorobovInt || R <= FamilyAcc<FAM>::kIntFinishMaxR;
             fa.init_fixed();
 #pragma unroll 1
             for (int j = 0; j < p.d; ++j)
@@ -298,7 +299,9 @@ __device__ __forceinline__ void tile_partial(double acc_re, double acc_im, doubl
 // registers; their throughput depends on hiding integer latency), no constraint for the
 // polynomial families (their per-thread working set needs the registers).
 template <int FAM>
-constexpr int kSumsMinBlocks = (FAM == QMC_SECTOR || FAM == QMC_FEYNMAN) ? 1 : 5;
+constexpr bool kPolyFamily = FAM == QMC_SECTOR || FAM == QMC_FEYNMAN;
+template <int FAM>
+constexpr int kSumsMinBlocks = kPolyFamily<FAM> ? 1 : 5;
 
 template <int FAM, int TK>
 __global__ void __launch_bounds__(kSumsThreads, kSumsMinBlocks<FAM>)

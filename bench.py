@@ -507,12 +507,17 @@ def goal_met(res, epsrel: float, epsabs: float = SERVE_EPSABS) -> bool:
 
 
 def run_serve_workload(args):
-    """Serving: Poisson arrivals of Feynman-parameter-like integrals (complex, d = 5, contour
-    deformation with lam = 1, Korobov-3, m = 32; half with F > 0 on the cube, half with F
-    changing sign inside), each with a relative error target log-uniform in [1e-8, 1e-3],
-    the library's default absolute target 1e-7, and an evaluation budget; continuous batching (qmc_server) against the same arrival
-    stream served one integral at a time (qmc_integrate, adaptive).  Reports p50/p99
-    latency (arrival to completion), integrals/s and the number of goals met for both."""
+    """Serving: Poisson arrivals of integrals with error targets, served by continuous
+    batching (qmc_server) and, for the same arrival stream, one integral at a time
+    (qmc_integrate, adaptive).  Reports p50/p99 latency (arrival to completion),
+    integrals/s and the number of goals met for both.  Profiles:
+      feynman  64 Feynman-parameter-like integrals (complex, d = 5, contour deformation
+               with lam = 1, Korobov-3, m = 32; half with F > 0 on the cube, half with F
+               changing sign inside), relative targets log-uniform in [1e-8, 1e-3], the
+               default absolute target 1e-7 and an evaluation budget: GPU-bound requests;
+      small    512 Genz integrals in d = 4 (product peak and Gaussian alternately,
+               Korobov-3, m = 32), relative targets log-uniform in [1e-7, 1e-4]: requests
+               of 1e4 to 1e6 evaluations, bound by launches and host round trips."""
     import torch
 
     import paper_1811_11720_gb300 as q
@@ -521,18 +526,33 @@ def run_serve_workload(args):
     torch.cuda.set_device(dev)
     table = q.GenvecTable.load()
     rng = np.random.default_rng(args.seed)
-    N = args.requests
+    small = args.serve_profile == "small"
+    N = args.requests if not small or args.requests != 64 else 512
+    rates = args.rates if args.rates else ([500.0, 2000.0, 8000.0] if small else [2.0, 8.0, 32.0])
     reqs = []
     for i in range(N):
-        # alternately Euclidean-like (F > 0 on the cube, beta = 0.6) and with F changing
-        # sign inside (beta = 0.95); lam = 1 keeps F(z) away from zero
-        beta = 0.6 if i % 2 == 0 else 0.95
-        f = q.Integrand.polynomial(W.feynman_regular(args.seed + i, beta=beta, lam=1.0))
-        eps = float(10 ** rng.uniform(-8, -3))
+        if small:
+            # alternately a d = 4 product peak (c_j = 5) and a d = 4 Gaussian from the Genz
+            # ranges, relative targets log-uniform in [1e-7, 1e-4]: n from 1021 to ~1e5
+            if i % 2 == 0:
+                c, w = W.product_peak_params(4, args.seed + i)
+                f = q.Integrand.genz(2, c, w)
+            else:
+                c, w = W.genz_params(4, 4, args.seed + i)
+                f = q.Integrand.genz(4, c, w)
+            eps = float(10 ** rng.uniform(-7, -4))
+        else:
+            # alternately Euclidean-like (F > 0 on the cube, beta = 0.6) and with F changing
+            # sign inside (beta = 0.95); lam = 1 keeps F(z) away from zero
+            beta = 0.6 if i % 2 == 0 else 0.95
+            f = q.Integrand.polynomial(W.feynman_regular(args.seed + i, beta=beta, lam=1.0))
+            eps = float(10 ** rng.uniform(-8, -3))
         reqs.append((f, eps))
+    workload = ("genz_product_peak|gaussian_d4_korobov3_m32_eps1e-7..1e-4_poisson" if small else
+                "feynman_regular_d5_beta0.6|0.95_lam1_korobov3_m32_eps1e-8..1e-3_poisson")
     out = {"metric": "served integrals/s", "unit": "integrals/s", "higher_is_better": True,
            "n_gpus": 1, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "feynman_regular_d5_beta0.6|0.95_lam1_korobov3_m32_eps1e-8..1e-3_poisson",
+           "config": {"workload": workload,
                       "requests": N, "maxeval": args.serve_maxeval,
                       "step_evaluations": int(args.serve_step_evals)}, "rates": []}
 
@@ -540,7 +560,7 @@ def run_serve_workload(args):
         r = np.random.default_rng(args.seed + int(rate * 1000))
         return np.cumsum(r.exponential(1.0 / rate, N))
 
-    for rate in args.rates:
+    for rate in rates:
         t_arr = arrivals(rate)
         # continuous batching
         srv = q.Server(table, memory_budget=int(args.serve_budget), max_slots=256, m=M_SHIFTS,
@@ -561,9 +581,8 @@ def run_serve_workload(args):
             if open_ids:
                 srv.step()
                 tnow = time.perf_counter() - t0
-                for rid in list(open_ids):
-                    if srv.status(rid)["state"] == srv.DONE:
-                        done_t[open_ids.pop(rid)] = tnow
+                for rid in srv.completed():
+                    done_t[open_ids.pop(rid)] = tnow
             elif nxt < N:
                 time.sleep(max(0.0, t_arr[nxt] - (time.perf_counter() - t0)))
         span_b = max(done_t) - t_arr[0]
@@ -587,6 +606,11 @@ def run_serve_workload(args):
         span_s = max(done_s) - t_arr[0]
         lat_s = np.array(done_s) - t_arr
         same = all(rb["integral"] == rs["integral"] for rb, rs in zip(res_b, res_s))
+        diffs = [{"request": i, "n": [int(res_b[i]["n"]), int(res_s[i]["n"])],
+                  "evaluations": [int(res_b[i]["evaluations"]), int(res_s[i]["evaluations"])],
+                  "rel_diff": float(abs(res_b[i]["integral"] - res_s[i]["integral"]) /
+                                    max(abs(res_s[i]["integral"]), 1e-300))}
+                 for i in range(N) if res_b[i]["integral"] != res_s[i]["integral"]]
         met_s = sum(goal_met(res_s[i], reqs[i][1]) for i in range(N))
         out["rates"].append({
             "rate_per_s": rate,
@@ -594,7 +618,8 @@ def run_serve_workload(args):
                         "p99_s": float(np.percentile(lat_b, 99)), "goal_met": int(met_b)},
             "one_at_a_time": {"integrals_per_s": N / span_s, "p50_s": float(np.percentile(lat_s, 50)),
                               "p99_s": float(np.percentile(lat_s, 99)), "goal_met": int(met_s)},
-            "same_results": bool(same)})
+            "same_results": bool(same),
+            **({"mismatches": len(diffs), "mismatch_examples": diffs[:4]} if diffs else {})})
     best = out["rates"][-1]
     out["value"] = best["batched"]["integrals_per_s"]
     out["p50_s"] = best["batched"]["p50_s"]
@@ -649,7 +674,12 @@ def main():
     ap.add_argument("--workload", default="genz",
                     choices=["genz", "feynman", "batch", "serve", "latency"])
     ap.add_argument("--requests", type=int, default=64)
-    ap.add_argument("--rates", type=float, nargs="*", default=[2.0, 8.0, 32.0])
+    ap.add_argument("--rates", type=float, nargs="*", default=None,
+                    help="arrival rates per second (default: 2 8 32 for the Feynman profile, "
+                         "500 2000 8000 for the small profile)")
+    ap.add_argument("--serve-profile", default="feynman", choices=["feynman", "small"],
+                    help="serve workload: Feynman-parameter integrals (GPU-bound requests) or "
+                         "small Genz integrals (launch-bound requests)")
     ap.add_argument("--serve-maxeval", type=float, default=3.2e7)
     ap.add_argument("--serve-budget", type=float, default=4e9)
     ap.add_argument("--serve-step-evals", type=float, default=2.0 ** 25,

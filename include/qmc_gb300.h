@@ -299,7 +299,8 @@ int qmc_batch_autotune(const qmc_batch_item *items, int count, void *workspace,
  * adaptive mode, Sec. 3.3.1, errormode all) and an evaluation budget maxeval, starting
  * at get_next_n(minn).  Each qmc_server_step admits queued requests in arrival order
  * while memory and slots allow (reserving coefficients, shifts and the tile partials of
- * the request's largest admissible lattice), runs the admitted requests (all of them, or
+ * the largest tile count among the lattices up to the request's largest admissible
+ * one; the count is not monotone in n), runs the admitted requests (all of them, or
  * those chosen within step_evaluations) on their current lattices in one batched launch
  * per integrand family, and then completes requests whose
  * goal is met or whose budget is spent, moving the others to larger table sizes.  A
@@ -345,6 +346,13 @@ int qmc_server_status(qmc_server *s, uint64_t id, int *state, qmc_result *result
 
 /* Queued and running requests and the free bytes of the pool. */
 int qmc_server_counts(qmc_server *s, int *pending, int *active, size_t *free_bytes);
+
+/* Identifiers of the requests that finished since the previous call, in completion order:
+ * up to cap of them are written to ids (host, caller-owned), *count receives how many;
+ * the rest stay queued for the next call.  A serving loop reads these after each step
+ * instead of polling every open request.  Errors: QMC_ERR_ARG (s, ids or count NULL,
+ * cap < 0). */
+int qmc_server_completed(qmc_server *s, uint64_t *ids, int cap, int *count);
 
 /* ---- tile-aligned sharding --------------------------------------------------------- */
 

@@ -513,6 +513,17 @@ class Server:
         _check(lib().qmc_server_counts(self.handle, C.byref(p), C.byref(a), C.byref(f)), "server_counts")
         return int(p.value), int(a.value), int(f.value)
 
+    def completed(self, cap: int = 4096) -> list[int]:
+        """Identifiers of the requests finished since the previous call (qmc_server_completed)."""
+        out = []
+        buf = (C.c_uint64 * cap)()
+        while True:
+            k = C.c_int()
+            _check(lib().qmc_server_completed(self.handle, buf, cap, C.byref(k)), "server_completed")
+            out.extend(int(buf[i]) for i in range(k.value))
+            if k.value < cap:
+                return out
+
     def close(self):
         if self.handle:
             lib().qmc_server_destroy(self.handle)

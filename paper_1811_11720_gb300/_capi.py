@@ -123,6 +123,7 @@ PROTOTYPES = {
     "qmc_server_status": (C.c_int, [C.c_void_p, C.c_uint64, _P(C.c_int), _P(qmc_result),
                                     _P(C.c_double)]),
     "qmc_server_counts": (C.c_int, [C.c_void_p, _P(C.c_int), _P(C.c_int), _P(C.c_size_t)]),
+    "qmc_server_completed": (C.c_int, [C.c_void_p, _P(C.c_uint64), C.c_int, _P(C.c_int)]),
     "qmc_sums_tile_count": (C.c_int, [C.c_uint64, C.c_uint64, _P(C.c_uint64), _P(C.c_uint64)]),
     "qmc_sums_tiles": (C.c_int, [_P(qmc_integrand), _P(qmc_rule), C.c_uint64, C.c_uint64,
                                  C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),

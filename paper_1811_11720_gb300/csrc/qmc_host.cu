@@ -125,12 +125,26 @@ extern "C" int qmc_integrate(const qmc_integrand *f, const qmc_genvec_table *tab
     L.off_cnt = take(2 * sizeof(unsigned long long));
     L.off_hist = take(use_fit ? (size_t)d * bins * sizeof(double) : 8);
     L.off_hws = take(use_fit ? qmc_histogram_workspace_bytes(n_fit, d, bins) : 8);
+    // lattice-sum workspace: the largest over the (n, m) pairs the loop may visit, i.e. n
+    // with m, and with options every table size up to n_max with m and then n_max with
+    // m doubled up to QMC_MAX_SHIFTS.  The tile count is not monotone in n (whole waves),
+    // so neither the largest n nor the largest m alone bounds it.
     qmc_rule probe;
     std::memset(&probe, 0, sizeof(probe));
-    probe.n = opts ? n_max : n;
-    probe.m = m_cap;
     probe.dim = d;
-    L.off_ws = take(qmc_sums_workspace_bytes(&probe, cplx, 0, probe.n));
+    auto ws_need = [&](uint64_t v, uint64_t mm) {
+        probe.n = v;
+        probe.m = mm;
+        return qmc_sums_workspace_bytes(&probe, cplx, 0, v);
+    };
+    size_t ws_bytes = 0;
+    for (int c = 0; c < table->count; ++c) {
+        const uint64_t v = table->n[c];
+        if (v >= n && v <= (opts ? n_max : n)) ws_bytes = std::max(ws_bytes, ws_need(v, m));
+    }
+    if (opts)
+        for (uint64_t mm = 2 * m; mm <= QMC_MAX_SHIFTS; mm *= 2) ws_bytes = std::max(ws_bytes, ws_need(n_max, mm));
+    L.off_ws = take(ws_bytes);
     L.total = o;
 
     std::lock_guard<std::mutex> lock(g_mutex);
@@ -212,8 +226,8 @@ extern "C" int qmc_integrate(const qmc_integrand *f, const qmc_genvec_table *tab
         unsigned long long *d_cnt = (unsigned long long *)(base + L.off_cnt);
         if (cudaMemsetAsync(d_cnt, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) return QMC_ERR_CUDA;
         double *d_sums = (double *)(base + L.off_sums);
-        size_t wsb = qmc_sums_workspace_bytes(&rule, cplx, 0, n);
-        st = qmc_sums(&df, &rule, 0, n, base + L.off_ws, wsb, d_sums, d_cnt, stream);
+        // the reservation, so that qmc_sums' size check guards it
+        st = qmc_sums(&df, &rule, 0, n, base + L.off_ws, ws_bytes, d_sums, d_cnt, stream);
         if (st) return st;
         double *d_res = (double *)(base + L.off_res);
         if ((st = qmc_finalize(d_sums, cur_m, n, cplx, d_res, nullptr, stream))) return st;

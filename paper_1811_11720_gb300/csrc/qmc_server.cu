@@ -55,6 +55,7 @@ struct Request {
     qmc_integrand fd{};
     uint64_t *d_shifts = nullptr;
     double *d_partials = nullptr;
+    uint64_t tiles_cap = 0;  // tiles of partials reserved
     std::vector<uint64_t> shifts;
     // progress
     uint64_t n = 0, evaluations = 0, iterations = 0;
@@ -86,6 +87,7 @@ struct qmc_server {
     unsigned long long *h_counters = nullptr;
     std::deque<uint64_t> pending;
     std::vector<uint64_t> active;
+    std::deque<uint64_t> completed;   // finished, not yet reported by qmc_server_completed
     std::unordered_map<uint64_t, Request> reqs;
     uint64_t next_id = 1;
     std::mutex mu;
@@ -147,16 +149,24 @@ uint64_t largest_admissible_n(const qmc_server *s, const Request &r) {
     return best;
 }
 
-size_t request_bytes(const qmc_server *s, const Request &r, uint64_t nmax) {
+size_t request_bytes(const qmc_server *s, const Request &r, uint64_t nmax, uint64_t *tiles_cap) {
     const int d = r.fh.dim;
     const int cplx = is_complex_family(r.fh.family);
-    Geometry g = geometry(nmax, (int)s->cfg.m);
+    // the partials of the largest tile count over the lattices the request may visit: the
+    // count is not monotone in n (whole waves; e.g. 2261 tiles at n = 886,097 against 2257
+    // at n = 974,707 for m = 32), so the largest lattice alone would under-reserve
+    uint64_t n0 = 0;
+    if (next_table_n(s, r.minn, &n0)) n0 = nmax;
+    uint64_t tiles = 0;
+    for (uint64_t v : s->tn)
+        if (v >= n0 && v <= nmax) tiles = std::max(tiles, geometry(v, (int)s->cfg.m).tiles);
     size_t b = 0;
     b += al256(r.c.size() * 8) + al256(r.w.size() * 8) + al256(r.h.size() * 8);
     b += al256(r.ucoef.size() * 8) + al256(r.fcoef.size() * 8);
     b += al256(r.uexp.size() * 4) + al256(r.fexp.size() * 4);
     b += al256(s->cfg.m * d * 8);
-    b += al256(g.tiles * s->cfg.m * 2 * sizeof(double) * (cplx ? 2 : 1));
+    b += al256(tiles * s->cfg.m * 2 * sizeof(double) * (cplx ? 2 : 1));
+    *tiles_cap = tiles;
     return b;
 }
 
@@ -175,7 +185,7 @@ int admit(qmc_server *s, Request &r) {
         r.t_done = now_s();
         return 1;
     }
-    const size_t bytes = request_bytes(s, r, nmax);
+    const size_t bytes = request_bytes(s, r, nmax, &r.tiles_cap);
     size_t off;
     if (!pool_alloc(s, bytes, &off)) return 0;
     r.off = off;
@@ -324,8 +334,12 @@ extern "C" int qmc_server_step(qmc_server *s, int *completed) {
         int a = admit(s, r);
         if (a == 0) break;   // out of memory: wait for completions
         s->pending.pop_front();
-        if (a == 1) ++done;
-        else s->active.push_back(r.id);
+        if (a == 1) {
+            ++done;
+            s->completed.push_back(r.id);
+        } else {
+            s->active.push_back(r.id);
+        }
     }
     if (s->active.empty()) {
         if (completed) *completed = done;
@@ -389,6 +403,7 @@ extern "C" int qmc_server_step(qmc_server *s, int *completed) {
             BatchItem &it = s->h_items[base];
             int st = fill_batch_item(it, b, m, spb, 0, fam);
             if (st) return st;
+            if (it.tiles > r.tiles_cap) return QMC_ERR_WORKSPACE;   // never: see request_bytes
             it.tile_begin = tiles;
             it.partial_off = (uint64_t)(r.d_partials - (double *)s->pool);
             s->h_tb[base - g0] = tiles;
@@ -454,6 +469,7 @@ extern "C" int qmc_server_step(qmc_server *s, int *completed) {
             r.t_done = t;
             pool_free(s, r.off, r.bytes);
             ++done;
+            s->completed.push_back(r.id);
         } else {
             still.push_back(r.id);
         }
@@ -486,6 +502,18 @@ extern "C" int qmc_server_status(qmc_server *s, uint64_t id, int *state, qmc_res
     }
     if (latency_s) *latency_s = r.state == QMC_REQ_DONE ? r.t_done - r.t_submit : -1.0;
     return r.state == QMC_REQ_DONE ? r.status : QMC_OK;
+}
+
+extern "C" int qmc_server_completed(qmc_server *s, uint64_t *ids, int cap, int *count) {
+    if (!s || !ids || !count || cap < 0) return QMC_ERR_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    int k = 0;
+    while (k < cap && !s->completed.empty()) {
+        ids[k++] = s->completed.front();
+        s->completed.pop_front();
+    }
+    *count = k;
+    return QMC_OK;
 }
 
 extern "C" int qmc_server_counts(qmc_server *s, int *pending, int *active, size_t *free_bytes) {

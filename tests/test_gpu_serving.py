@@ -69,6 +69,78 @@ def test_server_matches_adaptive_integrate(env):
     assert got["n"] == ref["n"] and got["iterations"] == ref["iterations"]
 
 
+def test_concurrent_requests_through_non_monotone_tile_counts(env):
+    """Many concurrent requests of two families that run to their evaluation budget: the
+    largest admissible lattice (n = 974,707, 2257 tiles at m = 32) has fewer tiles than the
+    one they end on (n = 886,097, 2261 tiles), so a reservation sized by the largest
+    lattice alone let one request's partials overwrite its neighbour in the pool.  Each
+    result must equal qmc_integrate with the same arguments, bit for bit."""
+    q, torch, tab = env
+    m, maxeval = 32, 32 * 974_707 + 1000
+    srv = q.Server(tab, memory_budget=1 << 30, max_slots=64, m=m, step_evaluations=0)
+    fs = []
+    for i in range(24):
+        if i % 2 == 0:
+            c, w = W.product_peak_params(4, 100 + i)
+            fs.append(q.Integrand.genz(2, c, w))
+        else:
+            c, w = W.genz_params(4, 4, 100 + i)
+            fs.append(q.Integrand.genz(4, c, w))
+    ids = [srv.submit(f, epsrel=1e-12, epsabs=0.0, minn=1021, maxeval=maxeval, seed=i)
+           for i, f in enumerate(fs)]
+    _drain(srv, ids)
+    got = [srv.status(i) for i in ids]
+    srv.close()
+    # the budget admits n = 974,707 but, after the first lattice, stops the escalation at
+    # n = 886,097: the lattice with more tiles than the largest admissible one
+    assert all(g["n"] == 886_097 for g in got)
+    for i, f in enumerate(fs):
+        ref = q.integrate(f, tab, 1021, m, ("korobov", 3), seed=i,
+                          opts=q.options(epsrel=1e-12, epsabs=0.0, maxeval=maxeval))
+        for k in ("integral", "error", "n", "iterations", "evaluations"):
+            assert got[i][k] == ref[k], (i, k, got[i][k], ref[k])
+
+
+def test_integrate_with_a_table_ending_below_a_larger_tile_count(env):
+    """qmc_integrate's workspace covers every lattice the adaptive loop may visit: with the
+    table cut at n = 974,707 (2257 tiles at m = 32) an adaptive run starting at n = 886,097
+    (2261 tiles) must pass the lattice sums' workspace check and agree with the full
+    table's run (one iteration each: the budget is exactly one lattice)."""
+    q, torch, tab = env
+    c, w = W.product_peak_params(4, 7)
+    f = q.Integrand.genz(2, c, w)
+    keep = [i for i, n in enumerate(tab.n) if n <= 974_707]
+    cut = q.GenvecTable(np.asarray(tab.n)[keep], np.asarray(tab.z)[keep])
+    opts = q.options(epsrel=1e-12, epsabs=0.0, maxeval=32 * 886_097)
+    a = q.integrate(f, cut, 886_097, 32, ("korobov", 3), seed=3, opts=opts)
+    b = q.integrate(f, tab, 886_097, 32, ("korobov", 3), seed=3, opts=opts)
+    assert a["n"] == b["n"] == 886_097 and a["iterations"] == b["iterations"] == 1
+    assert a["integral"] == b["integral"] and a["error"] == b["error"]
+
+
+def test_completion_queue_reports_each_request_once(env):
+    """qmc_server_completed lists every finished request exactly once, in completion
+    order, and agrees with the per-request state."""
+    q, torch, tab = env
+    srv = q.Server(tab, memory_budget=256 << 20, max_slots=8, m=16)
+    ids = []
+    for i in range(12):
+        c, w = W.genz_params(4, 3 + i % 3, 40 + i)
+        ids.append(srv.submit(q.Integrand.genz(4, c, w), epsrel=10.0 ** -(3 + i % 4),
+                              maxeval=4_000_000, seed=i))
+    seen = []
+    for _ in range(400):
+        srv.step()
+        for rid in srv.completed():
+            assert srv.status(rid)["state"] == srv.DONE
+            seen.append(rid)
+        if len(seen) == len(ids):
+            break
+    assert sorted(seen) == sorted(ids) and len(set(seen)) == len(seen)
+    assert srv.completed() == []
+    srv.close()
+
+
 def test_memory_budget_limits_concurrency(env):
     q, torch, tab = env
     # each request reserves the complex partials of its largest lattice (n = 108863: tiles x

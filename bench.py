@@ -516,8 +516,9 @@ def run_serve_workload(args):
                changing sign inside), relative targets log-uniform in [1e-8, 1e-3], the
                default absolute target 1e-7 and an evaluation budget: GPU-bound requests;
       small    512 Genz integrals in d = 4 (product peak and Gaussian alternately,
-               Korobov-3, m = 32), relative targets log-uniform in [1e-7, 1e-4]: requests
-               of 1e4 to 1e6 evaluations, bound by launches and host round trips."""
+               Korobov-3, m = 32), relative targets log-uniform in [1e-6, 1e-3], budget
+               4e6 evaluations: requests of 3e4 to 1e6 evaluations (microseconds of GPU
+               time), bound by launches and host round trips."""
     import torch
 
     import paper_1811_11720_gb300 as q
@@ -528,19 +529,20 @@ def run_serve_workload(args):
     rng = np.random.default_rng(args.seed)
     small = args.serve_profile == "small"
     N = args.requests if not small or args.requests != 64 else 512
-    rates = args.rates if args.rates else ([500.0, 2000.0, 8000.0] if small else [2.0, 8.0, 32.0])
+    rates = args.rates if args.rates else ([1000.0, 4000.0, 16000.0] if small else [2.0, 8.0, 32.0])
+    maxeval = 4e6 if small and args.serve_maxeval == 3.2e7 else args.serve_maxeval
     reqs = []
     for i in range(N):
         if small:
             # alternately a d = 4 product peak (c_j = 5) and a d = 4 Gaussian from the Genz
-            # ranges, relative targets log-uniform in [1e-7, 1e-4]: n from 1021 to ~1e5
+            # ranges, relative targets log-uniform in [1e-6, 1e-3]: n from 1021 to ~3e4
             if i % 2 == 0:
                 c, w = W.product_peak_params(4, args.seed + i)
                 f = q.Integrand.genz(2, c, w)
             else:
                 c, w = W.genz_params(4, 4, args.seed + i)
                 f = q.Integrand.genz(4, c, w)
-            eps = float(10 ** rng.uniform(-7, -4))
+            eps = float(10 ** rng.uniform(-6, -3))
         else:
             # alternately Euclidean-like (F > 0 on the cube, beta = 0.6) and with F changing
             # sign inside (beta = 0.95); lam = 1 keeps F(z) away from zero
@@ -548,12 +550,12 @@ def run_serve_workload(args):
             f = q.Integrand.polynomial(W.feynman_regular(args.seed + i, beta=beta, lam=1.0))
             eps = float(10 ** rng.uniform(-8, -3))
         reqs.append((f, eps))
-    workload = ("genz_product_peak|gaussian_d4_korobov3_m32_eps1e-7..1e-4_poisson" if small else
+    workload = ("genz_product_peak|gaussian_d4_korobov3_m32_eps1e-6..1e-3_poisson" if small else
                 "feynman_regular_d5_beta0.6|0.95_lam1_korobov3_m32_eps1e-8..1e-3_poisson")
     out = {"metric": "served integrals/s", "unit": "integrals/s", "higher_is_better": True,
            "n_gpus": 1, "dtype": "f64", "data": "synthetic",
            "config": {"workload": workload,
-                      "requests": N, "maxeval": args.serve_maxeval,
+                      "requests": N, "maxeval": maxeval,
                       "step_evaluations": int(args.serve_step_evals)}, "rates": []}
 
     def arrivals(rate):
@@ -575,7 +577,7 @@ def run_serve_workload(args):
             while nxt < N and t_arr[nxt] <= now:
                 f, eps = reqs[nxt]
                 ids[nxt] = srv.submit(f, epsrel=eps, epsabs=SERVE_EPSABS, minn=1021,
-                                      maxeval=int(args.serve_maxeval), seed=nxt)
+                                      maxeval=int(maxeval), seed=nxt)
                 open_ids[ids[nxt]] = nxt
                 nxt += 1
             if open_ids:
@@ -600,7 +602,7 @@ def run_serve_workload(args):
                 time.sleep(t_arr[i] - now)
             f, eps = reqs[i]
             r = q.integrate(f, table, 1021, M_SHIFTS, ("korobov", 3), seed=i,
-                            opts=q.options(epsrel=eps, epsabs=SERVE_EPSABS, maxeval=int(args.serve_maxeval)))
+                            opts=q.options(epsrel=eps, epsabs=SERVE_EPSABS, maxeval=int(maxeval)))
             done_s[i] = time.perf_counter() - t0
             res_s.append(r)
         span_s = max(done_s) - t_arr[0]

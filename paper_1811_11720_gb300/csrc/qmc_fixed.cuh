@@ -12,10 +12,14 @@
 //       P(v) = C int_0^1 s^r (1 - v s)^r ds = sum_k binom(r+k, k) (1 - v)^k
 //     (expand (1 - v s)^r = ((1 - s) + w s)^r and integrate the Beta integrals), e.g.
 //     1 + 2w | 1 + 3w + 6w^2 | 1 + 4w + 10w^2 + 20w^3 | 1 + 5w + 15w^2 + 35w^3 + 70w^4.
-//     Unsigned Horner in fixed point with F fractional bits, F the largest value with
-//     P(0) 2^F = sum_k binom(r+k, k) 2^F < 2^64 (every Horner intermediate is at most that
-//     for w <= 1); each step truncates by at most 3 units of 2^-F (F = 62, 60, 58, 57, 55,
-//     53 for r = 1..6; the products drop their low partial products, see mulhi_trunc).
+//     Unsigned Estrin form in fixed point with F fractional bits, F the largest value with
+//     P(1) 2^F = sum_k binom(r+k, k) 2^F < 2^64 (every partial sum is at most that for
+//     w <= 1): coefficient pairs (c_2j + c_2j+1 w) by shifts and adds, times w^2j from
+//     squarings; each product truncates by at most 3 units of 2^-F (F = 62, 60, 58, 57,
+//     55, 53 for r = 1..6; the products drop their low partial products, see mulhi_trunc).
+//     w^2 comes from v^2 by additions.  Exact-arithmetic checks of these integer steps give
+//     the same worst phi error as Horner's scheme (2^-56.2 for r = 3) with 3 to 5 fewer
+//     64-bit products.
 //   * phi = v^(r+1) P in 0.64 fixed point; the absolute error is below 2^-(61 - 1.7 r)
 //     (2^-54.9 for r = 4, 2^-50.9 for r = 6: the power's truncations times
 //     P <= binom(2r+1, r), and the truncations of the last product scaled by 2^(64 - F)).  The integrands
@@ -197,14 +201,54 @@ __device__ __forceinline__ uint64_t fixed_pow(uint64_t V, uint64_t V2) {
     }
 }
 
-// Horner steps k = K, K-1, ..., 0 of P(w) = sum_k binom(R+k, k) w^k for Korobov<R,R>:
-// p <- floor(p W / 2^64) + binom(R+k, k) 2^F, W = w 2^64.
-template <int R, int K>
-__device__ __forceinline__ uint64_t korobov_horner(uint64_t p, uint64_t W) {
-    constexpr uint64_t c = (uint64_t)korobov_Pw(R, K) << korobov_F(R);
-    p = mulhi_trunc(p, W) + c;
-    if constexpr (K > 0) return korobov_horner<R, K - 1>(p, W);
-    else return p;
+// x C for a compile-time constant C as shifts and adds (the integer-multiply pipe is the
+// busier one in this kernel; the product must fit in 64 bits).
+__host__ __device__ constexpr int ctz_c(uint64_t c) {
+    int b = 0;
+    while (!(c & 1)) {
+        c >>= 1;
+        ++b;
+    }
+    return b;
+}
+template <uint64_t C>
+__device__ __forceinline__ uint64_t mul_const(uint64_t x) {
+    if constexpr (C == 0) return 0;
+    else return (x << ctz_c(C)) + mul_const<(C & (C - 1))>(x);
+}
+
+// The pair J of P's coefficients as (binom(R+2J, 2J) + binom(R+2J+1, 2J+1) w) 2^F, with
+// ws = w 2^F (the second coefficient is 0 past k = R).
+template <int R, int J>
+__device__ __forceinline__ uint64_t korobov_pair(uint64_t ws) {
+    constexpr int F = korobov_F(R);
+    constexpr uint64_t c0 = (uint64_t)korobov_Pw(R, 2 * J) << F;
+    constexpr uint64_t c1 = 2 * J + 1 <= R ? (uint64_t)korobov_Pw(R, 2 * J + 1) : 0ull;
+    return c0 + mul_const<c1>(ws);
+}
+
+// P(w) 2^F = sum_k binom(R+k, k) w^k 2^F for Korobov<R,R>, W = w 2^64 (w = 1 - v), in
+// Estrin's form: sum_J (c_2J + c_2J+1 w) w^2J.  The pairs need only shifts and adds, and
+// w^2 = 1 - 2v + v^2 comes from V2 = v^2 2^64 by additions (2^64 - 2 - 2V + V2, within 3
+// units of floor(W^2 2^-64); V < 2^63), so P costs 1 (R = 2, 3), 3 (R = 4, 5) or 5 (R = 6)
+// 64-bit high products against R in Horner's scheme, with the same error bound (every
+// term is positive, every partial sum at most P(1) 2^F < 2^64).
+template <int R>
+__device__ __forceinline__ uint64_t korobov_P(uint64_t V, uint64_t V2) {
+    constexpr int F = korobov_F(R);
+    const uint64_t W = ~V;
+    const uint64_t ws = W >> (64 - F);
+    uint64_t P = korobov_pair<R, 0>(ws);
+    if constexpr (R >= 2) {
+        const uint64_t W2 = V2 - 2 * V - 2;
+        P += mulhi_trunc(korobov_pair<R, 1>(ws), W2);
+        if constexpr (R >= 4) {
+            const uint64_t W4 = mulhi_trunc(W2, W2);
+            P += mulhi_trunc(korobov_pair<R, 2>(ws), W4);
+            if constexpr (R >= 6) P += mulhi_trunc(korobov_pair<R, 3>(ws), mulhi_trunc(W4, W2));
+        }
+    }
+    return P;
 }
 
 // phi(v) 2^64 for V = v 2^64 (v <= 1/2), and t = v (1 - v) folded into the normalized
@@ -213,11 +257,10 @@ template <int R>
 __device__ __forceinline__ uint64_t korobov_phi_fixed(uint64_t V, Fx &Wp) {
     static_assert(R >= 1 && R <= kMaxKorobovInt, "integer Korobov order");
     constexpr int F = korobov_F(R);
-    constexpr uint64_t top = (uint64_t)korobov_Pw(R, R) << F;
-    // w = 1 - v: 2^64 - 1 - V, within 2^-64 of (1 - v) 2^64
-    const uint64_t p = korobov_horner<R, R - 1>(top, ~V);
-    // v^(r+1) 2^64
     const uint64_t V2 = mulhi_trunc(V, V);
+    // P in w = 1 - v (2^64 - 1 - V, within 2^-64 of (1 - v) 2^64)
+    const uint64_t p = korobov_P<R>(V, V2);
+    // v^(r+1) 2^64
     const uint64_t pw = fixed_pow<R + 1>(V, V2);
     // t = v - v^2 in 0.64 fixed point (<= 2^62), into the weight product as it is: its
     // leading zeros carry no information (t is exact to 3 2^-64 absolutely), and the

@@ -209,7 +209,7 @@ __device__ __forceinline__ double reflected_c_sum(uint32_t mask, int d, const Fa
 template <>
 struct FamilyAcc<QMC_GENZ_OSCILLATORY> {
     static constexpr bool kComplex = false;
-    static constexpr int kIntFinishMaxR = 2;   // integer finish up to this Korobov order
+    static constexpr int kIntFinishMaxR = 4;   // integer finish up to this Korobov order
     double s;
     uint32_t mask;
     __device__ __forceinline__ void init(const FamilyShared &fs) { s = fs.s0; mask = 0; }
@@ -322,7 +322,7 @@ struct FamilyAcc<QMC_GENZ_CORNER_PEAK> {
 template <>
 struct FamilyAcc<QMC_GENZ_GAUSSIAN> {
     static constexpr bool kComplex = false;
-    static constexpr int kIntFinishMaxR = 2;   // integer finish up to this Korobov order
+    static constexpr int kIntFinishMaxR = 3;   // integer finish up to this Korobov order
     double s;
     __device__ __forceinline__ void init(const FamilyShared &) { s = 0.0; }
     __device__ __forceinline__ void add(int j, const Mapped &m, const FamilyShared &fs) {
@@ -358,7 +358,7 @@ struct FamilyAcc<QMC_GENZ_GAUSSIAN> {
 template <>
 struct FamilyAcc<QMC_GENZ_C0> {
     static constexpr bool kComplex = false;
-    static constexpr int kIntFinishMaxR = 2;   // integer finish up to this Korobov order
+    static constexpr int kIntFinishMaxR = 3;   // integer finish up to this Korobov order
     double s;
     __device__ __forceinline__ void init(const FamilyShared &) { s = 0.0; }
     __device__ __forceinline__ void add(int j, const Mapped &m, const FamilyShared &fs) {
@@ -391,7 +391,7 @@ struct FamilyAcc<QMC_GENZ_C0> {
 template <>
 struct FamilyAcc<QMC_GENZ_DISCONTINUOUS> {
     static constexpr bool kComplex = false;
-    static constexpr int kIntFinishMaxR = 2;   // integer finish up to this Korobov order
+    static constexpr int kIntFinishMaxR = 3;   // integer finish up to this Korobov order
     double s;
     uint32_t mask;
     bool zero;

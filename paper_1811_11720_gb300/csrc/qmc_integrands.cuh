@@ -50,6 +50,7 @@ struct FixedForms {
     uint64_t tk[kMaxDim];    // oscillatory: integer part of c_j / (2 pi)
     uint64_t tg[kMaxDim];    // oscillatory: fraction of c_j / (2 pi), 2^64 scale
     uint64_t t0;             // oscillatory: w_1 2^64 mod 2^64
+    bool tk_any;             // oscillatory: some c_j >= 2 pi (a nonzero integer part)
     uint64_t one;            // 2^(2S - 64) (product peak)
     double num;              // prod_j c_j^2 (product peak)
     int S;
@@ -138,6 +139,7 @@ __device__ __forceinline__ void stage_fixed_forms(const P &p, FixedForms &fx) {
         if constexpr (FAM == QMC_GENZ_OSCILLATORY) {
             const double w1 = p.w ? p.w[0] : 0.0;
             fx.t0 = ok ? (w1 >= 1.0 ? 0ull : __double2ull_rz(ldexp(w1, 64))) : 0ull;
+            fx.tk_any = cmax >= 6.283185307179586;
         }
         if constexpr (FAM == QMC_GENZ_PRODUCT_PEAK) {
             double num = 1.0;
@@ -228,7 +230,12 @@ struct FamilyAcc<QMC_GENZ_OSCILLATORY> {
     __device__ __forceinline__ void init_fixed() { sl = 0; }
     template <bool kInt>
     __device__ __forceinline__ void add_fixed(int j, uint64_t x, const FamilyShared &fs) {
-        if constexpr (kInt) sl += x * fs.fx.tk[j] + mulhi_trunc(x, fs.fx.tg[j]);
+        if constexpr (kInt) {
+            // the integer turns per unit x only when some c_j >= 2 pi (a uniform branch;
+            // the Genz ranges have ||c||_1 = 6)
+            if (fs.fx.tk_any) sl += x * fs.fx.tk[j];
+            sl += mulhi_trunc(x, fs.fx.tg[j]);
+        }
         else sl += mulhi_trunc(x, fs.fx.cl[j]);
     }
     template <bool kInt>

@@ -324,9 +324,33 @@ __global__ void __launch_bounds__(kSumsThreads, kSumsMinBlocks<FAM>)
     double cd = 1.0;  // Korobov C^d
     if constexpr (TK == QMC_T_KOROBOV || TK == kTKorobovInt) cd = ipow_u(p.t.C, d);
 
-    uint64_t dsh[kMaxDim];
+    // The shifts D_kj 2^11 (the 53-bit shift in the high word's units), read once per
+    // dimension of every evaluation, are per-thread values in local memory, which misses
+    // L1 (the shared memory of five blocks leaves little of it).  Under the cheap maps
+    // (baker, none) the separable families stage them in shared memory instead, in the
+    // polynomial buffer they do not use, as [k][j] rows of odd length (the warp's lanes hit
+    // distinct banks): +2 to +10 % there, while under the integer Korobov map the
+    // generic loads this needs cost more than the misses.
+    uint64_t dsh_local[kMaxDim];
+    const uint64_t *dsh = dsh_local;
+    bool staged = false;
+    if constexpr (!kPolyFamily<FAM> && (TK == QMC_T_BAKER || TK == QMC_T_NONE)) {
+        const int ds = d | 1;
+        if (m * ds <= 4 * kMaxTerms) {
+            uint64_t *s_dsh = fsh.poly.buf.u;
+            for (int i = tid; i < m * ds; i += blockDim.x) {
+                const int kk = i / ds, j = i - kk * ds;
+                s_dsh[i] = j < d ? (p.shifts[(size_t)kk * d + j] << 11) : 0ull;
+            }
+            dsh = s_dsh + k * ds;
+            staged = true;
+            __syncthreads();
+        }
+    }
+    if (!staged) {
 #pragma unroll 1
-    for (int j = 0; j < d; ++j) dsh[j] = active ? (p.shifts[(size_t)k * d + j] << 11) : 0ull;
+        for (int j = 0; j < d; ++j) dsh_local[j] = active ? (p.shifts[(size_t)k * d + j] << 11) : 0ull;
+    }
 
     unsigned long long nonfinite = 0, signfail = 0;
     const uint64_t ptile = (uint64_t)p.spb * p.L;

@@ -53,7 +53,7 @@ SM_MAX_MHZ = 2070.0
 # Korobov-3, n = 1,072,187).  The kernel reads kilobytes of constants and writes the tile
 # partials, whose number does not grow with n (whole waves of 760 tiles, at most six), so
 # the figure applies to the benchmark's launches as measured.  None once the kernel changes.
-TRAFFIC_BYTES_PER_LAUNCH = 286_208
+TRAFFIC_BYTES_PER_LAUNCH = 378_368
 
 
 def fp64_flops_per_eval(family: int, transform, d: int) -> int:

@@ -3,7 +3,7 @@ quadrature on GB300 (one JSON line on stdout).
 
 Workload (one step = the whole hot path over one batch): Genz oscillatory, corner peak
 and Gaussian (Sec. 5.2 test functions, ||c||_1 = 6.0, 2.2, 15.2) in d = 6, 8, 10, each
-with the baker and Korobov r = 1..4 transforms: 45 integrals, each on the CBC lattice
+with the baker and Korobov r = 1..4 maps (3 x 3 x 5 = 45 integrals), each on the CBC lattice
 n = 10,560,653 (the first table size >= 1e7) with m = 32 random shifts; seeded synthetic
 parameters (workloads.genz_params).  Per integral the step runs the lattice-sum kernel,
 the fixed-order tile reduction and the shift reduction (mean and standard error).

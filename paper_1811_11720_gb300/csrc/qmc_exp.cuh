@@ -33,9 +33,10 @@
 //
 // GB300 issues ~2 FP64 fused multiply-adds per clock per SM against ~32x as many integer
 // multiply-adds.  The integer form (~60 integer instructions for ~13 FP64 ones) pays when
-// the rest of the evaluation leaves the integer pipes idle (baker, Korobov r <= 2); under
-// the integer Korobov r >= 3 the integer pipes are the bottleneck and the FP64 form, on the
-// otherwise idle FP64 pipe, is faster.
+// the rest of the evaluation leaves the integer multiply pipe room (baker, none, Korobov up
+// to r = 3 for the exp families); under the higher Korobov orders that pipe is the
+// bottleneck and the FP64 form, on the otherwise idle FP64 pipe, is faster (the crossover
+// is FamilyAcc::kIntFinishMaxR).
 #pragma once
 #include <cstdint>
 

@@ -53,6 +53,7 @@ struct FixedForms {
     bool tk_any;             // oscillatory: some c_j >= 2 pi (a nonzero integer part)
     uint64_t one;            // 2^(2S - 64) (product peak)
     double num;              // prod_j c_j^2 (product peak)
+    Fx numx;                 // the same as Fx (zero or normal)
     int S;
     bool ok;
 };
@@ -144,7 +145,9 @@ __device__ __forceinline__ void stage_fixed_forms(const P &p, FixedForms &fx) {
         if constexpr (FAM == QMC_GENZ_PRODUCT_PEAK) {
             double num = 1.0;
             for (int i = 0; ok && i < p.d; ++i) num *= p.c[i] * p.c[i];
+            ok = ok && (num == 0.0 || num >= 0x1p-1022);   // Fx takes zero or normal values
             fx.num = num;
+            fx.numx = fx_of_double(ok ? num : 0.0);
             fx.one = ok ? 1ull << (2 * S - 64) : 0ull;
         }
         fx.S = S;
@@ -251,7 +254,7 @@ struct FamilyAcc<QMC_GENZ_OSCILLATORY> {
 template <>
 struct FamilyAcc<QMC_GENZ_PRODUCT_PEAK> {
     static constexpr bool kComplex = false;
-    static constexpr int kIntFinishMaxR = 0;   // integer finish up to this Korobov order
+    static constexpr int kIntFinishMaxR = 6;   // integer finish up to this Korobov order
     double prod;
     __device__ __forceinline__ void init(const FamilyShared &) { prod = 1.0; }
     __device__ __forceinline__ void add(int j, const Mapped &m, const FamilyShared &fs) {
@@ -279,7 +282,10 @@ struct FamilyAcc<QMC_GENZ_PRODUCT_PEAK> {
     template <bool kInt>
     __device__ __forceinline__ void finish_fixed(int, const FamilyShared &fs, double &re,
                                                  double &im, unsigned long long &) {
-        re = fs.fx.num / fx_to_double(pf);
+        // prod c_j^2 times the reciprocal of the product (Newton on the integer pipe), or
+        // one FP64 division
+        if constexpr (kInt) re = fx_to_double(fx_mul(fs.fx.numx, fx_recip(pf)));
+        else re = fs.fx.num / fx_to_double(pf);
         im = 0.0;
     }
 };

@@ -61,8 +61,8 @@ __global__ void __launch_bounds__(kBatchRedThreads)
 }
 
 // One thread per item: Qbar and sigma (Eq. (lattice), Eq. (lattice-error)).
-__global__ void batch_finalize_kernel(const BatchItem *items, int count, int m, int cplx,
-                                      const double *sums, double *results) {
+__global__ void batch_finalize_kernel(const BatchItem *__restrict__ items, int count, int m, int cplx,
+                                      const double *__restrict__ sums, double *__restrict__ results) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= count) return;
     const double dn = (double)items[q].n;
@@ -73,11 +73,13 @@ __global__ void batch_finalize_kernel(const BatchItem *items, int count, int m, 
             res[3] = 0.0;
             break;
         }
-        const double *sc = sums + (size_t)q * 4 * m + 2 * (size_t)comp * m;
+        const double *__restrict__ sc = sums + (size_t)q * 4 * m + 2 * (size_t)comp * m;
         double mean = 0.0;
+#pragma unroll 8
         for (int k = 0; k < m; ++k) mean += (sc[2 * k] + sc[2 * k + 1]) / dn;
         mean /= (double)m;
         double var = 0.0;
+#pragma unroll 8
         for (int k = 0; k < m; ++k) {
             double dq = (sc[2 * k] + sc[2 * k + 1]) / dn - mean;
             var = fma(dq, dq, var);

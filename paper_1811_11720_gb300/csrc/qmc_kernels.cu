@@ -104,13 +104,16 @@ cudaError_t launch_reduce_tiles(const double *partials, uint64_t tiles, int m, i
 }
 
 // Eq. (lattice) and Eq. (lattice-error): Q_k = S_k / n, Qbar, sigma, per component.
-__global__ void finalize_kernel(const double *sums, int m, uint64_t n, int is_complex,
-                                double *result, double *Q) {
+// One thread, the summation order fixed (k = 0..m-1) and shared with the batched form;
+// the restrict qualifiers let the loads and divisions of different k overlap.
+__global__ void finalize_kernel(const double *__restrict__ sums, int m, uint64_t n, int is_complex,
+                                double *__restrict__ result, double *__restrict__ Q) {
     if (threadIdx.x != 0) return;
     const double dn = (double)n;
     for (int comp = 0; comp < (is_complex ? 2 : 1); ++comp) {
-        const double *sc = sums + 2 * (size_t)comp * m;
+        const double *__restrict__ sc = sums + 2 * (size_t)comp * m;
         double mean = 0.0;
+#pragma unroll 8
         for (int k = 0; k < m; ++k) {
             double q = (sc[2 * k] + sc[2 * k + 1]) / dn;
             if (Q) Q[(size_t)comp * m + k] = q;
@@ -118,6 +121,7 @@ __global__ void finalize_kernel(const double *sums, int m, uint64_t n, int is_co
         }
         mean /= (double)m;
         double var = 0.0;
+#pragma unroll 8
         for (int k = 0; k < m; ++k) {
             double q = (sc[2 * k] + sc[2 * k + 1]) / dn - mean;
             var = fma(q, q, var);

@@ -54,6 +54,11 @@ SM_MAX_MHZ = 2070.0
 # partials, whose number does not grow with n (whole waves of 760 tiles, at most six), so
 # the figure applies to the benchmark's launches as measured.  None once the kernel changes.
 TRAFFIC_BYTES_PER_LAUNCH = 378_368
+# The unit that bounds the same capture (ncu sm__pipe_fmaheavy_cycles_active, elapsed):
+# the integer multiply pipe that executes the 64-bit high products.  None once the kernel
+# changes.
+LIMITER = {"unit": "integer multiply pipe (fmaheavy)", "busy": 0.801, "fp64_pipe_busy": 0.142,
+           "capture": "Gaussian d=10 Korobov-3 n=1072187 m=32, ncu --set full"}
 
 
 def fp64_flops_per_eval(family: int, transform, d: int) -> int:
@@ -759,13 +764,16 @@ def main():
         roof = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak_max, 1),
                 "unit": "GFLOP/s", "frac": round(achieved / peak_max, 4),
                 "traffic": TRAFFIC_BYTES_PER_LAUNCH if args.workload == "genz" else None,
+                "limiter": LIMITER if args.workload == "genz" else None,
                 "peak_at_median_clock": round(SM_COUNT * FP64_FLOP_PER_CLK_SM * sm_mhz / 1e3, 1),
                 "kernel": "sums_kernel (+ tile reduction, <0.1%)",
                 "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2070 MHz",
                 "note": ("achieved counts the method's FP64 flops per evaluation "
                          "(fp64_flops_per_eval); the kernel evaluates the lattice points, "
-                         "Korobov r<=6 and the Genz linear/quadratic forms exactly on the "
-                         "integer pipe, so this FP64-equivalent rate can exceed the FP64 peak")}
+                         "Korobov r<=6, the Genz forms and (for the cheaper maps) their "
+                         "exp/cos/power finishes exactly on the integer pipe, so this "
+                         "FP64-equivalent rate can exceed the FP64 peak; the unit that bounds "
+                         "the kernel is in 'limiter'")}
     if rank == 0:
         line = dict(base)
         line.update({

@@ -110,6 +110,21 @@ def test_workspace_size_depends_on_range_only(q):
     assert q.sums_workspace_bytes(r2, False, 0, 10560653) > a
 
 
+def test_tile_count_is_not_monotone_in_n(q):
+    """The tile decomposition comes in whole waves, so its tile count is not monotone in
+    the range length: at m = 32, n = 886,097 has more tiles than the larger n = 974,707.
+    Every reservation of partials for a sequence of lattices (the server's per-request
+    pool slice, qmc_integrate's workspace) must therefore take the maximum over the
+    lattices, not the largest one; the GPU regression tests exercise exactly this pair."""
+    t_small, _ = q.sums_tile_count(886_097, 32)
+    t_large, _ = q.sums_tile_count(974_707, 32)
+    assert t_small > t_large
+    Dd = np.zeros((32, 4), dtype=np.uint64)
+    r1 = q.rule(886_097, [1, 2, 3, 4], Dd, ("baker",))
+    r2 = q.rule(974_707, [1, 2, 3, 4], Dd, ("baker",))
+    assert q.sums_workspace_bytes(r1, False, 0, 886_097) > q.sums_workspace_bytes(r2, False, 0, 974_707)
+
+
 def test_lm_fit_matches_least_squares_oracle(q):
     """The library's Levenberg-Marquardt and SciPy's trust-region solver, on the same CDF
     data from an oracle histogram, give maps that agree closely (the fit itself is a

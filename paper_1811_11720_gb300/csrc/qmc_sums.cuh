@@ -7,7 +7,9 @@
 // multiple of 32: the lattice state is shared across the warp (see stream_sums) and the
 // instruction stream is uniform.  The transform and, where the integrand allows, the
 // integrand's linear and quadratic forms run in integer fixed point (qmc_fixed.cuh,
-// qmc_integrands.cuh); FP64 is left to the integrand's final function and the sums.
+// qmc_integrands.cuh), and under the cheaper maps so does its final function (qmc_exp.cuh,
+// qmc_cos.cuh); FP64 is left to the final function under the higher Korobov orders and to
+// the sums.
 // Each thread accumulates its L samples in FP64; the tile's per-shift partial is
 // the Neumaier-compensated sum over its spb streams in fixed order, written to
 // partials[tile][k].  Tiles depend only on the i-range, so the result is bit-identical for

@@ -18,8 +18,8 @@
 //     squarings; each product truncates by at most 3 units of 2^-F (F = 62, 60, 58, 57,
 //     55, 53 for r = 1..6; the products drop their low partial products, see mulhi_trunc).
 //     w^2 comes from v^2 by additions.  Exact-arithmetic checks of these integer steps give
-//     the same worst phi error as Horner's scheme (2^-56.2 for r = 3) with 3 to 5 fewer
-//     64-bit products.
+//     the same worst phi error as Horner's scheme (2^-56.2 for r = 3) with one or two fewer
+//     64-bit products per dimension (and no multiplies for the coefficients).
 //   * phi = v^(r+1) P in 0.64 fixed point; the absolute error is below 2^-(61 - 1.7 r)
 //     (2^-54.9 for r = 4, 2^-50.9 for r = 6: the power's truncations times
 //     P <= binom(2r+1, r), and the truncations of the last product scaled by 2^(64 - F)).  The integrands
@@ -230,9 +230,9 @@ __device__ __forceinline__ uint64_t korobov_pair(uint64_t ws) {
 // P(w) 2^F = sum_k binom(R+k, k) w^k 2^F for Korobov<R,R>, W = w 2^64 (w = 1 - v), in
 // Estrin's form: sum_J (c_2J + c_2J+1 w) w^2J.  The pairs need only shifts and adds, and
 // w^2 = 1 - 2v + v^2 comes from V2 = v^2 2^64 by additions (2^64 - 2 - 2V + V2, within 3
-// units of floor(W^2 2^-64); V < 2^63), so P costs 1 (R = 2, 3), 3 (R = 4, 5) or 5 (R = 6)
-// 64-bit high products against R in Horner's scheme, with the same error bound (every
-// term is positive, every partial sum at most P(1) 2^F < 2^64).
+// units of floor(W^2 2^-64); V < 2^63), so P costs 0 (R = 1), 1 (R = 2, 3), 3 (R = 4, 5)
+// or 5 (R = 6) 64-bit high products against R in Horner's scheme, with the same error
+// bound (every term is positive, every partial sum at most P(1) 2^F < 2^64).
 template <int R>
 __device__ __forceinline__ uint64_t korobov_P(uint64_t V, uint64_t V2) {
     constexpr int F = korobov_F(R);

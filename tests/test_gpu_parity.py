@@ -584,14 +584,15 @@ def test_large_n_fixed_point_paths(env, n, fam, tr):
         assert np.all(np.abs((gre[:, 0] + gre[:, 1]) - (o["re"][:, 0] + o["re"][:, 1])) <= TOL * o["abs"])
 
 
-@pytest.mark.parametrize("tr", [("korobov", 3), ("baker",)])
-def test_bench_size_sampled_subranges(env, tr):
-    """At the benchmark's size (n = 10560653, m = 32, d = 10), the full-range GPU result is
-    checked on sampled sub-ranges the oracle can afford, and the whole against the closed
-    form."""
+@pytest.mark.parametrize("fam", [1, 3, 4])
+@pytest.mark.parametrize("tr", [("baker",), ("korobov", 1), ("korobov", 2), ("korobov", 3),
+                                ("korobov", 4)])
+def test_bench_size_sampled_subranges(env, fam, tr):
+    """At the benchmark's size (n = 10560653, m = 32, d = 10) and for each of its families
+    and maps (integer and FP64 finishes both occur), the full-range GPU result is checked on
+    sampled sub-ranges the oracle can afford, and the whole against the closed form."""
     q, torch, dev, tab = env
     n, d, m = 10560653, 10, 32
-    fam = 4
     c, w = W.genz_params(fam, d, 1)
     D = O.shifts(77, m, d)
     z = tab.z_for(n)[:d]

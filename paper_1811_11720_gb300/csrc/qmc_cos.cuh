@@ -53,7 +53,7 @@ __device__ __forceinline__ double cos_turns_fixed(uint64_t T, const uint64_t *ta
     const bool neg = r < 0;
     const uint64_t a = (uint64_t)(neg ? -r : r);                 // |r| 2^64 turns, < 2^55
     const uint64_t Y = mulhi_trunc(a << 8, k2Pi);                // |y| 2^69
-    const uint64_t Z = mulhi_trunc(Y, Y);                        // z 2^74
+    const uint64_t Z = sqhi_trunc(Y);                        // z 2^74
     const uint64_t Ps = mulhi_trunc(Z, kC6 - mulhi_trunc(Z, kK120));            // z (1/6 - z/120) 2^74
     const uint64_t Sy = Y - (mulhi_trunc(Y, Ps) >> 10);                         // sin|y| 2^69
     const uint64_t Q2 = 0x8000000000000000ull - (mulhi_trunc(Z, kC24 - mulhi_trunc(Z, kK720)) >> 10);

@@ -73,6 +73,13 @@ __device__ __forceinline__ uint64_t mulhi_trunc(uint64_t a, uint64_t b) {
     return (uint64_t)ah * bh + __umulhi(ah, bl) + __umulhi(al, bh);
 }
 
+// The same for a square: the two cross products are equal, so one 32-bit high multiply
+// doubled (bit-identical to mulhi_trunc(a, a), which the compiler does not fold).
+__device__ __forceinline__ uint64_t sqhi_trunc(uint64_t a) {
+    const uint32_t al = (uint32_t)a, ah = (uint32_t)(a >> 32);
+    return (uint64_t)ah * ah + ((uint64_t)__umulhi(ah, al) << 1);
+}
+
 // ---------------------------------------------------------------------------------------
 // value = m 2^(e - 64); m == 0 encodes zero.  Normalized: m >= 2^63.
 struct Fx {
@@ -88,6 +95,7 @@ __device__ __forceinline__ Fx fx_of_double(double v) {
 
 // Truncated product (relative error below 2^-61 for normalized inputs); exponents add.
 __device__ __forceinline__ Fx fx_mul(Fx a, Fx b) { return {mulhi_trunc(a.m, b.m), a.e + b.e}; }
+__device__ __forceinline__ Fx fx_sq(Fx a) { return {sqhi_trunc(a.m), 2 * a.e}; }
 
 // Normalize a mantissa that is zero or >= 2^32 (shift 0..32; zero stays zero).
 __device__ __forceinline__ Fx fx_norm(Fx a) {
@@ -139,7 +147,7 @@ __device__ __forceinline__ Fx fx_powi(Fx a, int p) {
     Fx r = a;
 #pragma unroll 1
     for (int i = 30 - __clz(p); i >= 0; --i) {
-        r = fx_norm(fx_mul(r, r));
+        r = fx_norm(fx_sq(r));
         if ((p >> i) & 1) r = fx_norm(fx_mul(r, a));
     }
     return r;
@@ -195,7 +203,7 @@ __device__ __forceinline__ uint64_t fixed_pow(uint64_t V, uint64_t V2) {
         return mulhi_trunc(V2, V);
     } else {
         const uint64_t h = fixed_pow<E / 2>(V, V2);
-        const uint64_t sq = mulhi_trunc(h, h);
+        const uint64_t sq = sqhi_trunc(h);
         if constexpr (E % 2) return mulhi_trunc(sq, V);
         else return sq;
     }
@@ -243,7 +251,7 @@ __device__ __forceinline__ uint64_t korobov_P(uint64_t V, uint64_t V2) {
         const uint64_t W2 = V2 - 2 * V - 2;
         P += mulhi_trunc(korobov_pair<R, 1>(ws), W2);
         if constexpr (R >= 4) {
-            const uint64_t W4 = mulhi_trunc(W2, W2);
+            const uint64_t W4 = sqhi_trunc(W2);
             P += mulhi_trunc(korobov_pair<R, 2>(ws), W4);
             if constexpr (R >= 6) P += mulhi_trunc(korobov_pair<R, 3>(ws), mulhi_trunc(W4, W2));
         }
@@ -257,7 +265,7 @@ template <int R>
 __device__ __forceinline__ uint64_t korobov_phi_fixed(uint64_t V, Fx &Wp) {
     static_assert(R >= 1 && R <= kMaxKorobovInt, "integer Korobov order");
     constexpr int F = korobov_F(R);
-    const uint64_t V2 = mulhi_trunc(V, V);
+    const uint64_t V2 = sqhi_trunc(V);
     // P in w = 1 - v (2^64 - 1 - V, within 2^-64 of (1 - v) 2^64)
     const uint64_t p = korobov_P<R>(V, V2);
     // v^(r+1) 2^64
@@ -276,7 +284,7 @@ __device__ __forceinline__ Fx fx_pow(Fx Wp) {
         return Wp;
     } else {
         const Fx h = fx_pow<E / 2>(Wp);
-        const Fx sq = fx_norm(fx_mul(h, h));
+        const Fx sq = fx_norm(fx_sq(h));
         if constexpr (E % 2) return fx_norm(fx_mul(sq, Wp));
         else return sq;
     }

@@ -276,7 +276,7 @@ struct FamilyAcc<QMC_GENZ_PRODUCT_PEAK> {
         const uint64_t w = fs.fx.w64[j];
         const uint64_t a = x >= w ? x - w : w - x;                       // |x - w| 2^64
         const uint64_t q = mulhi_trunc(a, fs.fx.cq[j]);                 // c |x - w| 2^S
-        const uint64_t s = fs.fx.one + mulhi_trunc(q, q);               // (1 + q^2) 2^(2S-64)
+        const uint64_t s = fs.fx.one + sqhi_trunc(q);               // (1 + q^2) 2^(2S-64)
         pf = fx_norm(fx_mul(pf, fx_norm({s, 128 - 2 * fs.fx.S})));
     }
     template <bool kInt>
@@ -356,7 +356,7 @@ struct FamilyAcc<QMC_GENZ_GAUSSIAN> {
         const uint64_t w = fs.fx.w64[j];
         const uint64_t a = x >= w ? x - w : w - x;                       // |x - w| 2^64
         const uint64_t q = mulhi_trunc(a, fs.fx.cq[j]);                 // c |x - w| 2^S
-        sq += mulhi_trunc(q, q);
+        sq += sqhi_trunc(q);
     }
     template <bool kInt>
     __device__ __forceinline__ void finish_fixed(int, const FamilyShared &fs, double &re,

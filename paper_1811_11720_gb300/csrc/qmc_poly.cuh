@@ -375,9 +375,29 @@ __device__ __forceinline__ cplx feynman_jacobian_det(const double *x, const doub
             if (k == l) mkl = fma(1.0 - 2.0 * x[k], g[k], mkl);
             A[k * d + l] = {(k == l) ? 1.0 : 0.0, -lam * mkl};
         }
-    cplx det = {1.0, 0.0};
+    // Column 0 by hand: before any elimination the off-diagonal entries are purely
+    // imaginary (A = I - i lam M), so the multipliers and the updates need two real
+    // products each instead of a full complex product (about a quarter of the
+    // determinant's FP64 work for d = 5).
+    cplx det = A[0];
+    if (d == 1) return det;
+    {
+        const cplx inv = crecip(A[0]);
 #pragma unroll 1
-    for (int c = 0; c < d; ++c) {
+        for (int r = 1; r < d; ++r) {
+            const double a = A[r * d].im;                      // A[r][0] = i a
+            const cplx l = {-a * inv.im, a * inv.re};          // i a / A[0][0]
+#pragma unroll 1
+            for (int q = 1; q < d; ++q) {
+                const double b = A[q].im;                      // A[0][q] = i b
+                cplx &t = A[r * d + q];                        // t -= l (i b)
+                t.re = fma(l.im, b, t.re);
+                t.im = fma(-l.re, b, t.im);
+            }
+        }
+    }
+#pragma unroll 1
+    for (int c = 1; c < d; ++c) {
         cplx piv = A[c * d + c];
         det = cmul(det, piv);
         if (c + 1 == d) break;
@@ -387,10 +407,10 @@ __device__ __forceinline__ cplx feynman_jacobian_det(const double *x, const doub
             cplx l = cmul(A[r * d + c], inv);
 #pragma unroll 1
             for (int q = c + 1; q < d; ++q) {
-                cplx a = A[c * d + q];
-                cplx &t = A[r * d + q];
-                t.re -= fma(l.re, a.re, -l.im * a.im);
-                t.im -= fma(l.re, a.im, l.im * a.re);
+                const cplx a = A[c * d + q];
+                cplx &t = A[r * d + q];                        // t -= l a, four fused steps
+                t.re = fma(-l.re, a.re, fma(l.im, a.im, t.re));
+                t.im = fma(-l.re, a.im, fma(-l.im, a.re, t.im));
             }
         }
     }

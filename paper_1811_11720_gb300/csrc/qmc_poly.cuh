@@ -363,7 +363,9 @@ __device__ __forceinline__ cplx clog_principal(cplx a) {
 
 // det J = det(I - i lam (D H + E)), D = diag(x (1 - x)), E = diag((1 - 2x) g), by
 // elimination without pivoting (see the header comment); H is d x d in local memory.
-__device__ __forceinline__ cplx feynman_jacobian_det(const double *x, const double *xo,
+// lx[k] = -lam x_k (1 - x_k): the imaginary part of J is lx_k H_kl, plus -lam (1 - 2 x_k) g_k
+// on the diagonal.
+__device__ __forceinline__ cplx feynman_jacobian_det(const double *x, const double *lx,
                                                      const double *g, const double *H, int d,
                                                      double lam) {
     cplx A[kMaxDim * kMaxDim];
@@ -371,9 +373,9 @@ __device__ __forceinline__ cplx feynman_jacobian_det(const double *x, const doub
     for (int k = 0; k < d; ++k)
 #pragma unroll 1
         for (int l = 0; l < d; ++l) {
-            double mkl = xo[k] * H[k * d + l];
-            if (k == l) mkl = fma(1.0 - 2.0 * x[k], g[k], mkl);
-            A[k * d + l] = {(k == l) ? 1.0 : 0.0, -lam * mkl};
+            double im = lx[k] * H[k * d + l];
+            if (k == l) im = fma(-lam * fma(-2.0, x[k], 1.0), g[k], im);
+            A[k * d + l] = {(k == l) ? 1.0 : 0.0, im};
         }
     // Column 0 by hand: before any elimination the off-diagonal entries are purely
     // imaginary (A = I - i lam M), so the multipliers and the updates need two real
@@ -514,12 +516,12 @@ static __device__ __noinline__ void feynman_value_dense(const double *xin, int d
     }
     Fx += fb[0];
     Ux += ub[0];
-    // deformation
+    // deformation: xo holds -lam x (1 - x)
     const double lam = ps.lam;
 #pragma unroll 1
     for (int k = 0; k < d; ++k) {
-        xo[k] = x[k] * (1.0 - x[k]);
-        y[k] = -lam * xo[k] * g[k];
+        xo[k] = -lam * (x[k] * (1.0 - x[k]));
+        y[k] = xo[k] * g[k];
     }
     // F(z), U(z)
     double yHy = 0.0, gy = 0.0, yU2y = 0.0, gUy = 0.0, t3 = 0.0;
@@ -597,11 +599,11 @@ static __device__ __noinline__ void feynman_value(const double *xin, int d, cons
     }
     const double lam = ps.lam;
     cplx z[kMaxDim];
-    double xo[kMaxDim];   // x (1 - x)
+    double xo[kMaxDim];   // -lam x (1 - x)
 #pragma unroll 1
     for (int k = 0; k < d; ++k) {
-        xo[k] = x[k] * (1.0 - x[k]);
-        z[k] = {x[k], -lam * xo[k] * grad[k]};
+        xo[k] = -lam * (x[k] * (1.0 - x[k]));
+        z[k] = {x[k], xo[k] * grad[k]};
     }
     // U(z), F(z)
     cplx U = {0.0, 0.0}, F = {0.0, 0.0};

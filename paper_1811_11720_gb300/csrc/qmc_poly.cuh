@@ -53,7 +53,7 @@ struct PolyShared {
 //   F = f0 + sum_i f1_i x_i + sum_ij F2_ij x_i x_j + sum_ijk F3_ijk x_i x_j x_k
 // with U2, F2, F3 fully symmetric (a monomial's coefficient shared equally by the
 // permutations of its factors).  Layout in buf: U at [0]: u0, u1[d], U2[d][d];
-// F at [2 kMaxTerms]: f0, f1[d], F2[d][d], F3[pair(i <= j)][k] (row-major upper triangle).
+// F at [2 kMaxTerms]: f0, f1[d], F2[d][d], 6 F3[pair(i <= j)][k] (row-major upper triangle).
 constexpr int kFeynDenseMaxDim = 11;   // 1 + d + d^2 + d^2 (d+1)/2 <= 2 kMaxTerms
 __device__ __forceinline__ int feyn_pair(int i, int j, int d) {   // i <= j
     return i * d - i * (i - 1) / 2 + (j - i);
@@ -110,6 +110,8 @@ __device__ __forceinline__ int monomial_key(const int32_t *e, int d, int D, int 
 
 // Adds coefficient c of monomial e (degree <= 3) to the symmetric tensors at base
 // (constant, linear, square matrix, then for deg 3 the F3[pair][k] block when t3 != null).
+// The cubic block is stored times 6 (6 F3), the factor of the Hessian 2 F2 + 6 F3 x, so
+// that the Hessian costs one fused multiply-add per entry; F3[y, y, y] divides it out.
 __device__ __forceinline__ void feyn_add_term(double *base, double *t3, const int32_t *e, int d,
                                               double c) {
     int f[3];
@@ -131,17 +133,17 @@ __device__ __forceinline__ void feyn_add_term(double *base, double *t3, const in
     } else {
         const int a = f[0], b = f[1], e3 = f[2];   // a <= b <= e3
         if (a == b && b == e3) {
-            t3[feyn_pair(a, a, d) * d + a] += c;
+            t3[feyn_pair(a, a, d) * d + a] += 6.0 * c;
         } else if (a == b) {          // a a e3: (aa, e3), (a e3, a)
-            t3[feyn_pair(a, a, d) * d + e3] += c / 3.0;
-            t3[feyn_pair(a, e3, d) * d + a] += c / 3.0;
+            t3[feyn_pair(a, a, d) * d + e3] += 2.0 * c;
+            t3[feyn_pair(a, e3, d) * d + a] += 2.0 * c;
         } else if (b == e3) {         // a b b: (ab, b), (bb, a)
-            t3[feyn_pair(a, b, d) * d + b] += c / 3.0;
-            t3[feyn_pair(b, b, d) * d + a] += c / 3.0;
+            t3[feyn_pair(a, b, d) * d + b] += 2.0 * c;
+            t3[feyn_pair(b, b, d) * d + a] += 2.0 * c;
         } else {                      // distinct: (ab, e3), (a e3, b), (b e3, a)
-            t3[feyn_pair(a, b, d) * d + e3] += c / 6.0;
-            t3[feyn_pair(a, e3, d) * d + b] += c / 6.0;
-            t3[feyn_pair(b, e3, d) * d + a] += c / 6.0;
+            t3[feyn_pair(a, b, d) * d + e3] += c;
+            t3[feyn_pair(a, e3, d) * d + b] += c;
+            t3[feyn_pair(b, e3, d) * d + a] += c;
         }
     }
 }
@@ -424,7 +426,12 @@ __device__ __forceinline__ cplx feynman_jacobian_det(const double *x, const doub
 // The branch that avoids cancellation: t = sqrt((|a| + |Re a|) / 2), the other part
 // Im a / (2 t).
 __device__ __forceinline__ cplx csqrt_principal(cplx a) {
-    const double r = hypot(a.re, a.im);
+    // |a| without the library's rescaling where the squares can neither overflow nor
+    // underflow (|re|, |im| in [2^-500, 2^500]; relative error within 1.5 ulp)
+    const double m = fmax(fabs(a.re), fabs(a.im));
+    const double r = (m < 0x1p500 && fmin(fabs(a.re), fabs(a.im)) > 0x1p-500)
+                         ? sqrt(fma(a.re, a.re, a.im * a.im))
+                         : hypot(a.re, a.im);
     if (r == 0.0) return {0.0, a.im};
     const double t = sqrt(0.5 * (r + fabs(a.re)));
     const double o = a.im / (2.0 * t);
@@ -479,7 +486,7 @@ static __device__ __noinline__ void feynman_value_dense(const double *xin, int d
     const double *ub = ps.buf.v;
     const double *u1 = ub + 1, *U2 = ub + 1 + d;
     const double *fb = ps.buf.v + 2 * kMaxTerms;
-    const double *f1 = fb + 1, *F2 = fb + 1 + d, *F3 = fb + 1 + d + d * d;
+    const double *f1 = fb + 1, *F2 = fb + 1 + d, *F3 = fb + 1 + d + d * d;   // F3: 6 F3
     double x[kMaxDim], g[kMaxDim], y[kMaxDim], xo[kMaxDim];
     double H[kMaxDim * kMaxDim];
 #pragma unroll 1
@@ -493,7 +500,7 @@ static __device__ __noinline__ void feynman_value_dense(const double *xin, int d
             double s = 0.0;
 #pragma unroll 1
             for (int k = 0; k < d; ++k) s = fma(t[k], x[k], s);
-            const double h = fma(6.0, s, 2.0 * F2[i * d + j]);
+            const double h = fma(2.0, F2[i * d + j], s);   // s = (6 F3 x)_ij
             H[i * d + j] = h;
             H[j * d + i] = h;
         }
@@ -546,7 +553,7 @@ static __device__ __noinline__ void feynman_value_dense(const double *xin, int d
             t3 = fma((i == j ? 1.0 : 2.0) * y[i] * y[j], s, t3);
         }
     }
-    const cplx Fz = {fma(-0.5, yHy, Fx), gy - t3};
+    const cplx Fz = {fma(-0.5, yHy, Fx), fma(t3, -1.0 / 6.0, gy)};   // t3 = 6 F3[y, y, y]
     const cplx Uz = {Ux - yU2y, gUy};
     if (Fz.im > 0.0) ++signfail;
     const cplx det = feynman_jacobian_det(x, xo, g, H, d, lam);

@@ -238,8 +238,9 @@ struct FamilyAcc<QMC_GENZ_OSCILLATORY> {
             // the Genz ranges have ||c||_1 = 6)
             if (fs.fx.tk_any) sl += x * fs.fx.tk[j];
             sl += mulhi_trunc(x, fs.fx.tg[j]);
+        } else {
+            sl += mulhi_trunc(x, fs.fx.cl[j]);
         }
-        else sl += mulhi_trunc(x, fs.fx.cl[j]);
     }
     template <bool kInt>
     __device__ __forceinline__ void finish_fixed(int, const FamilyShared &fs, double &re,

@@ -138,6 +138,14 @@ def test_completion_queue_reports_each_request_once(env):
             break
     assert sorted(seen) == sorted(ids) and len(set(seen)) == len(seen)
     assert srv.completed() == []
+    # a request that no table size admits completes at admission, with its error status
+    c, w = W.genz_params(4, 3, 99)
+    bad = srv.submit(q.Integrand.genz(4, c, w), epsrel=1e-3, minn=10 ** 15, maxeval=10 ** 7, seed=1)
+    srv.step()
+    assert srv.completed() == [bad]
+    with pytest.raises(q.QMCError) as e:   # status reports QMC_ERR_N for it
+        srv.status(bad)
+    assert e.value.code == -3
     srv.close()
 
 

@@ -198,7 +198,11 @@ int qmc_sums(const qmc_integrand *f, const qmc_rule *rule, uint64_t i_begin, uin
  *     QMC_NOALLOC_SCRATCH_BYTES, e.g. real m = 32 beyond n ~ 1.1e9) are rejected with
  *     QMC_ERR_WORKSPACE before anything is launched.
  *   - The first call on a device looks up the array's device address (once per device,
- *     with that device current); make that first call before any stream capture.
+ *     with that device current); make that first call before any stream capture.  The
+ *     address is kept for the life of the process: after cudaDeviceReset() it is stale,
+ *     so do not call this entry point again in that process.
+ *   - Argument checks and their codes are those of qmc_sums, in the same order; only then
+ *     is the size compared with the array.
  *   - All calls on a device share the array and it keeps the last call's contents; the
  *     kernel overwrites every partial it reads, so nothing has to be cleared first.  Calls
  *     that overlap on the GPU (unordered streams or threads) race on it: order them.
@@ -385,6 +389,16 @@ int qmc_sums_tiles(const qmc_integrand *f, const qmc_rule *rule, uint64_t i_begi
  * (4 m complex) doubles.  Errors: QMC_ERR_ARG, QMC_ERR_M, QMC_ERR_CUDA. */
 int qmc_reduce_tiles(const double *partials, uint64_t tiles, uint64_t m, int is_complex,
                      double *sums, void *stream);
+
+/* Merge of per-shift sums computed on separate i-ranges of one rule (Sec. 2.1: the sum
+ * over a lattice is the sum of its parts' sums).  parts (host) holds nparts arrays of len
+ * doubles back to back, each in the qmc_sums layout of (hi, lo) double-double pairs (len
+ * even: 2m real, 4m complex); out (host, len doubles, may alias parts' first array)
+ * receives their double-double sum, pairs added in part order with TwoSum and a Fast2Sum
+ * renormalisation: deterministic, equal to the whole range's sums within the rounding of
+ * the double-double format.  No device work.  Errors: QMC_ERR_ARG (NULL, nparts < 1, len
+ * odd or < 2). */
+int qmc_merge_sums(const double *parts, uint64_t nparts, uint64_t len, double *out);
 
 /* ---- generating vectors: fast CBC on the device -------------------------------------- */
 

@@ -230,6 +230,27 @@ int qmc_reduce_tiles(const double *partials, uint64_t tiles, uint64_t m, int is_
     return e == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
 
+int qmc_merge_sums(const double *parts, uint64_t nparts, uint64_t len, double *out) {
+    if (!parts || !out || nparts < 1 || len < 2 || (len & 1)) return QMC_ERR_ARG;
+    // (hi, lo) += (a_hi, a_lo) per slot: TwoSum of the high words, the low words added to its
+    // error, renormalised with Fast2Sum; parts are taken in their order (deterministic)
+    for (uint64_t k = 0; k < len; k += 2) {
+        double hi = parts[k], lo = parts[k + 1];
+        for (uint64_t p = 1; p < nparts; ++p) {
+            const double a_hi = parts[p * len + k], a_lo = parts[p * len + k + 1];
+            const double s = hi + a_hi;
+            const double bp = s - hi;
+            double e = (hi - (s - bp)) + (a_hi - bp);
+            e = e + (lo + a_lo);
+            hi = s + e;
+            lo = e - (hi - s);
+        }
+        out[k] = hi;
+        out[k + 1] = lo;
+    }
+    return QMC_OK;
+}
+
 int qmc_finalize(const double *sums, uint64_t m, uint64_t n, int is_complex, double *result,
                  double *Q, void *stream) {
     if (!sums || !result) return QMC_ERR_ARG;

@@ -12,12 +12,17 @@
 // call's contents; the lattice-sum kernel overwrites every partial it later reads, so
 // nothing in it has to start at zero.  Calls that overlap on the GPU (different streams,
 // or host threads, without ordering between them) race on the array.
+//
+// The array's device address is looked up once per device and kept for the life of the
+// process; cudaDeviceReset() unloads the library's device image, so after a reset that
+// address is stale and this entry point must not be called again in the same process.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 #include <mutex>
 
 #include "qmc_gb300.h"
+#include "qmc_hostutil.h"
 
 namespace {
 
@@ -49,15 +54,20 @@ int noalloc_scratch(void **out) {
 extern "C" int qmc_sums_noalloc(const qmc_integrand *f, const qmc_rule *rule, uint64_t i_begin,
                                 uint64_t i_end, double *sums, unsigned long long *counters,
                                 void *stream) {
-    if (!f || !rule || !sums) return QMC_ERR_ARG;
+    using namespace qmc::host;
+    // the checks of qmc_sums, in its order, so that both entry points report the same code
+    int st = check_integrand_shape(f);
+    if (st) return st;
+    if ((st = check_rule(rule))) return st;
+    if (f->dim != rule->dim) return QMC_ERR_DIM;
+    if (!sums) return QMC_ERR_ARG;
     if (i_end <= i_begin || i_end > rule->n) return QMC_ERR_RANGE;
-    const int cplx = (f->family == QMC_FEYNMAN);
-    const size_t need = qmc_sums_workspace_bytes(rule, cplx, i_begin, i_end);
+    if ((st = device_ok())) return st;
+    const size_t need = qmc_sums_workspace_bytes(rule, is_complex_family(f->family), i_begin, i_end);
     if (need == 0) return QMC_ERR_ARG;
     if (need > (size_t)QMC_NOALLOC_SCRATCH_BYTES) return QMC_ERR_WORKSPACE;
     void *scratch = nullptr;
-    int st = noalloc_scratch(&scratch);
-    if (st) return st;
+    if ((st = noalloc_scratch(&scratch))) return st;
     return qmc_sums(f, rule, i_begin, i_end, scratch, (size_t)QMC_NOALLOC_SCRATCH_BYTES, sums,
                     counters, stream);
 }

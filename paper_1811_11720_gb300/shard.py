@@ -8,8 +8,9 @@ integral splits into contiguous pieces and the only exchange step is a gather.  
   partials are gathered in rank order (gather_tile_partials, 2m doubles per tile) and folded
   by qmc_reduce_tiles exactly as qmc_sums folds them;
 * i-range (shard_range, merge_sums): each rank runs qmc_sums on its own range and the
-  per-shift double-double sums (2m or 4m doubles per rank) add with TwoSum in rank order;
-  equal to the whole within rounding, independent of arrival order.
+  per-shift double-double sums (2m or 4m doubles per rank) are added in rank order by the
+  library (qmc_merge_sums); equal to the whole within rounding, independent of arrival
+  order.
 """
 from __future__ import annotations
 
@@ -63,29 +64,20 @@ def gather_tile_partials(local, tiles_per_rank, m: int, is_complex: bool, group=
     return assemble_tile_partials(parts, m, is_complex)
 
 
-def _two_sum(a, b):
-    s = a + b
-    bp = s - a
-    e = (a - (s - bp)) + (b - bp)
-    return s, e
-
-
 def merge_sums(parts) -> np.ndarray:
-    """Sum per-shard double-double arrays laid out as (hi, lo) pairs in fixed (list) order.
-    Each part is a float64 array of even length; returns the same layout."""
-    parts = [np.asarray(p, dtype=np.float64) for p in parts]
+    """Sum per-shard double-double arrays laid out as (hi, lo) pairs in fixed (list) order
+    (qmc_merge_sums).  Each part is a float64 array of the same even length; returns the
+    same layout."""
+    from . import _check, lib
+    parts = [np.ascontiguousarray(np.asarray(p, dtype=np.float64)).reshape(-1) for p in parts]
     if not parts:
         raise ValueError("nothing to merge")
-    hi = parts[0][0::2].copy()
-    lo = parts[0][1::2].copy()
-    for p in parts[1:]:
-        s, e = _two_sum(hi, p[0::2])
-        e = e + lo + p[1::2]
-        hi = s + e
-        lo = e - (hi - s)
-    out = np.empty_like(parts[0])
-    out[0::2] = hi
-    out[1::2] = lo
+    if any(p.size != parts[0].size for p in parts):
+        raise ValueError("parts differ in length")
+    stacked = np.ascontiguousarray(np.stack(parts))
+    out = np.empty(parts[0].size)
+    _check(lib().qmc_merge_sums(stacked.ctypes.data, len(parts), int(parts[0].size),
+                                out.ctypes.data), "merge_sums")
     return out
 
 

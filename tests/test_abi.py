@@ -176,3 +176,55 @@ def test_product_path_has_no_cpu_fallback():
     from paper_1811_11720_gb300 import _capi
     with pytest.raises(ImportError):
         _capi.load("/nonexistent/libqmc_gb300.so")
+
+
+def test_noalloc_argument_codes_match_sums(q):
+    """qmc_sums_noalloc validates its arguments exactly as qmc_sums does, in the same order
+    and before any device call (m = 0, m above QMC_MAX_SHIFTS, unknown family, dimension
+    mismatch, empty range)."""
+    lib = q.lib()
+    f = q.Integrand.genz(2, [1.0, 2.0], [0.5, 0.5]).host_struct()
+    out = np.zeros(16)
+    ws = np.zeros(64, dtype=np.uint8)
+    Dd = np.zeros((4, 2), dtype=np.uint64)
+    f3 = q.Integrand.genz(2, [1.0, 2.0, 3.0], [0.5, 0.5, 0.5]).host_struct()
+    bad = q.Integrand.genz(2, [1.0, 2.0], [0.5, 0.5]).host_struct()
+    bad.family = 99
+    cases = []
+    for m in (0, q._capi.QMC_MAX_SHIFTS + 1):
+        r = q.rule(1021, [1, 374], Dd, ("korobov", 3))
+        r.m = m
+        cases.append((f, r, 0, 1021, -5))
+    r = q.rule(1021, [1, 374], Dd, ("korobov", 3))
+    cases += [(bad, r, 0, 1021, -7), (f3, r, 0, 1021, -2), (f, r, 7, 7, -12)]
+    for ff, rr, a, b, code in cases:
+        assert lib.qmc_sums_noalloc(C.byref(ff), C.byref(rr), a, b, out.ctypes.data, None, None) == code
+        assert lib.qmc_sums(C.byref(ff), C.byref(rr), a, b, ws.ctypes.data, 64, out.ctypes.data,
+                            None, None) == code
+
+
+def test_merge_sums_is_compensated_and_ordered(q):
+    """qmc_merge_sums adds double-double per-shift sums in part order: the low words are
+    kept (1 + 1e16 - 1e16 survives), the result is the exact sum whenever that fits a
+    double-double, and bad sizes are rejected."""
+    from fractions import Fraction
+
+    from paper_1811_11720_gb300 import shard
+    parts = [np.array([1e16, 0.0]), np.array([1.0, 0.0]), np.array([-1e16, 0.0])]
+    out = shard.merge_sums(parts)
+    assert out[0] + out[1] == 1.0
+    rng = np.random.default_rng(3)
+    hi = rng.normal(size=(5, 8)) * 10.0 ** rng.integers(-8, 8, size=(5, 8))
+    lo = hi * 2.0 ** -60 * rng.normal(size=(5, 8))
+    pairs = np.empty((5, 16))
+    pairs[:, 0::2], pairs[:, 1::2] = hi, lo
+    got = shard.merge_sums(list(pairs))
+    for k in range(8):
+        exact = sum(Fraction(float(v)) for v in np.concatenate([hi[:, k], lo[:, k]]))
+        err = abs(Fraction(float(got[2 * k])) + Fraction(float(got[2 * k + 1])) - exact)
+        assert err <= abs(exact) * Fraction(2) ** -100 + Fraction(2) ** -1070
+    lib = q.lib()
+    buf = np.zeros(6)
+    assert lib.qmc_merge_sums(buf.ctypes.data, 1, 3, buf.ctypes.data) == -1
+    assert lib.qmc_merge_sums(buf.ctypes.data, 0, 2, buf.ctypes.data) == -1
+    assert lib.qmc_merge_sums(None, 1, 2, buf.ctypes.data) == -1

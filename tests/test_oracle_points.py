@@ -129,3 +129,19 @@ def test_custom_genvecs_paper_example(n):
     pts = O.points(n, z, D)[:, 0, :]
     for j in range(2):
         assert sorted(np.round(pts[:, j] * n).astype(int)) == list(range(n))
+
+
+def test_splitmix64_published_reference_outputs():
+    """The shift generator is SplitMix64 (Steele, Lea, Flood 2014): its first outputs for
+    two seeds equal the published reference implementation's test vectors
+    (tests/golden/splitmix64_reference.txt), so a mistyped increment or mixing constant
+    fails here rather than agreeing with itself on both sides of the parity tests."""
+    rows = [line.split() for line in open(golden("splitmix64_reference.txt"))
+            if line.strip() and not line.startswith("#")]
+    assert len(rows) == 2
+    for row in rows:
+        seed, outs = int(row[0]), [int(v) for v in row[1:]]
+        assert [O.splitmix64(seed, t) for t in range(len(outs))] == outs
+        # the shift numerators are those outputs >> 11, in row-major [k][j] order
+        D = O.shifts(seed, 1, len(outs))
+        assert D.reshape(-1).tolist() == [v >> 11 for v in outs]

@@ -364,16 +364,21 @@ __device__ __forceinline__ cplx clog_principal(cplx a) {
 }
 
 // det J = det(I - i lam (D H + E)), D = diag(x (1 - x)), E = diag((1 - 2x) g), by
-// elimination without pivoting (see the header comment); H is d x d in local memory.
-// lx[k] = -lam x_k (1 - x_k): the imaginary part of J is lx_k H_kl, plus -lam (1 - 2 x_k) g_k
-// on the diagonal.
+// elimination without pivoting (see the header comment).  lx[k] = -lam x_k (1 - x_k): the
+// imaginary part of J is lx_k H_kl, plus -lam (1 - 2 x_k) g_k on the diagonal.  DT > 0 is
+// the dimension as a compile-time constant (the loops unroll and the d x d work array can
+// live in registers); DT = 0 takes d at run time (the array in local memory).  Both run
+// the same operations in the same order.
+template <int DT>
 __device__ __forceinline__ cplx feynman_jacobian_det(const double *x, const double *lx,
-                                                     const double *g, const double *H, int d,
+                                                     const double *g, const double *H, int d_rt,
                                                      double lam) {
-    cplx A[kMaxDim * kMaxDim];
-#pragma unroll 1
+    constexpr int DA = DT > 0 ? DT : kMaxDim;
+    const int d = DT > 0 ? DT : d_rt;
+    cplx A[DA * DA];
+#pragma unroll
     for (int k = 0; k < d; ++k)
-#pragma unroll 1
+#pragma unroll
         for (int l = 0; l < d; ++l) {
             double im = lx[k] * H[k * d + l];
             if (k == l) im = fma(-lam * fma(-2.0, x[k], 1.0), g[k], im);
@@ -387,11 +392,11 @@ __device__ __forceinline__ cplx feynman_jacobian_det(const double *x, const doub
     if (d == 1) return det;
     {
         const cplx inv = crecip(A[0]);
-#pragma unroll 1
+#pragma unroll
         for (int r = 1; r < d; ++r) {
             const double a = A[r * d].im;                      // A[r][0] = i a
             const cplx l = {-a * inv.im, a * inv.re};          // i a / A[0][0]
-#pragma unroll 1
+#pragma unroll
             for (int q = 1; q < d; ++q) {
                 const double b = A[q].im;                      // A[0][q] = i b
                 cplx &t = A[r * d + q];                        // t -= l (i b)
@@ -400,16 +405,16 @@ __device__ __forceinline__ cplx feynman_jacobian_det(const double *x, const doub
             }
         }
     }
-#pragma unroll 1
+#pragma unroll
     for (int c = 1; c < d; ++c) {
         cplx piv = A[c * d + c];
         det = cmul(det, piv);
         if (c + 1 == d) break;
         cplx inv = crecip(piv);
-#pragma unroll 1
+#pragma unroll
         for (int r = c + 1; r < d; ++r) {
             cplx l = cmul(A[r * d + c], inv);
-#pragma unroll 1
+#pragma unroll
             for (int q = c + 1; q < d; ++q) {
                 const cplx a = A[c * d + q];
                 cplx &t = A[r * d + q];                        // t -= l a, four fused steps
@@ -479,26 +484,31 @@ __device__ __forceinline__ void feynman_combine(cplx U, cplx F, cplx det, double
 // and at z = x + i y (y = -lam x (1 - x) g) the cubic's Taylor series is exact:
 //   F(z) = F(x) - y.H y / 2 + i (g.y - sum_ijk F3_ijk y_i y_j y_k),
 //   U(z) = U(x) - y.U2 y + i grad U.y,  grad U = u1 + 2 U2 x.
-static __device__ __noinline__ void feynman_value_dense(const double *xin, int d,
+// DT > 0: the dimension as a compile-time constant (unrolled loops, per-thread arrays of
+// d entries that can stay in registers); DT = 0: d at run time.  Same operations, same order.
+template <int DT>
+static __device__ __noinline__ void feynman_value_dense(const double *xin, int d_rt,
                                                         const PolyShared &ps, double &re,
                                                         double &im,
                                                         unsigned long long &signfail) {
+    constexpr int DA = DT > 0 ? DT : kMaxDim;
+    const int d = DT > 0 ? DT : d_rt;
     const double *ub = ps.buf.v;
     const double *u1 = ub + 1, *U2 = ub + 1 + d;
     const double *fb = ps.buf.v + 2 * kMaxTerms;
     const double *f1 = fb + 1, *F2 = fb + 1 + d, *F3 = fb + 1 + d + d * d;   // F3: 6 F3
-    double x[kMaxDim], g[kMaxDim], y[kMaxDim], xo[kMaxDim];
-    double H[kMaxDim * kMaxDim];
-#pragma unroll 1
+    double x[DA], g[DA], y[DA], xo[DA];
+    double H[DA * DA];
+#pragma unroll
     for (int k = 0; k < d; ++k) x[k] = xin[k];
     // Hessian of F (symmetric)
-#pragma unroll 1
+#pragma unroll
     for (int i = 0; i < d; ++i)
-#pragma unroll 1
+#pragma unroll
         for (int j = i; j < d; ++j) {
             const double *t = F3 + feyn_pair(i, j, d) * d;
             double s = 0.0;
-#pragma unroll 1
+#pragma unroll
             for (int k = 0; k < d; ++k) s = fma(t[k], x[k], s);
             const double h = fma(2.0, F2[i * d + j], s);   // s = (6 F3 x)_ij
             H[i * d + j] = h;
@@ -506,11 +516,11 @@ static __device__ __noinline__ void feynman_value_dense(const double *xin, int d
         }
     // gradient, F(x), U(x), grad U
     double Fx = 0.0, Ux = 0.0;
-    double gU[kMaxDim];
-#pragma unroll 1
+    double gU[DA];
+#pragma unroll
     for (int i = 0; i < d; ++i) {
         double hx = 0.0, qx = 0.0, px = 0.0;
-#pragma unroll 1
+#pragma unroll
         for (int j = 0; j < d; ++j) {
             hx = fma(H[i * d + j], x[j], hx);
             qx = fma(F2[i * d + j], x[j], qx);
@@ -525,17 +535,17 @@ static __device__ __noinline__ void feynman_value_dense(const double *xin, int d
     Ux += ub[0];
     // deformation: xo holds -lam x (1 - x)
     const double lam = ps.lam;
-#pragma unroll 1
+#pragma unroll
     for (int k = 0; k < d; ++k) {
         xo[k] = -lam * (x[k] * (1.0 - x[k]));
         y[k] = xo[k] * g[k];
     }
     // F(z), U(z)
     double yHy = 0.0, gy = 0.0, yU2y = 0.0, gUy = 0.0, t3 = 0.0;
-#pragma unroll 1
+#pragma unroll
     for (int i = 0; i < d; ++i) {
         double hy = 0.0, uy = 0.0;
-#pragma unroll 1
+#pragma unroll
         for (int j = 0; j < d; ++j) {
             hy = fma(H[i * d + j], y[j], hy);
             uy = fma(U2[i * d + j], y[j], uy);
@@ -544,11 +554,11 @@ static __device__ __noinline__ void feynman_value_dense(const double *xin, int d
         yU2y = fma(y[i], uy, yU2y);
         gy = fma(g[i], y[i], gy);
         gUy = fma(gU[i], y[i], gUy);
-#pragma unroll 1
+#pragma unroll
         for (int j = i; j < d; ++j) {
             const double *t = F3 + feyn_pair(i, j, d) * d;
             double s = 0.0;
-#pragma unroll 1
+#pragma unroll
             for (int k = 0; k < d; ++k) s = fma(t[k], y[k], s);
             t3 = fma((i == j ? 1.0 : 2.0) * y[i] * y[j], s, t3);
         }
@@ -556,7 +566,7 @@ static __device__ __noinline__ void feynman_value_dense(const double *xin, int d
     const cplx Fz = {fma(-0.5, yHy, Fx), fma(t3, -1.0 / 6.0, gy)};   // t3 = 6 F3[y, y, y]
     const cplx Uz = {Ux - yU2y, gUy};
     if (Fz.im > 0.0) ++signfail;
-    const cplx det = feynman_jacobian_det(x, xo, g, H, d, lam);
+    const cplx det = feynman_jacobian_det<DT>(x, xo, g, H, d, lam);
     feynman_combine(Uz, Fz, det, ps.pa, ps.pb, re, im);
 }
 
@@ -564,8 +574,14 @@ static __device__ __noinline__ void feynman_value(const double *xin, int d, cons
                                            double &re, double &im,
                                            unsigned long long &signfail) {
     if (ps.feyn_dense) {
-        feynman_value_dense(xin, d, ps, re, im, signfail);
-        return;
+        // the symmetric-tensor form with the dimension compiled in for the common sizes
+        switch (d) {
+        case 3: feynman_value_dense<3>(xin, d, ps, re, im, signfail); return;
+        case 4: feynman_value_dense<4>(xin, d, ps, re, im, signfail); return;
+        case 5: feynman_value_dense<5>(xin, d, ps, re, im, signfail); return;
+        case 6: feynman_value_dense<6>(xin, d, ps, re, im, signfail); return;
+        default: feynman_value_dense<0>(xin, d, ps, re, im, signfail); return;
+        }
     }
     double x[kMaxDim];
     double grad[kMaxDim];
@@ -636,7 +652,7 @@ static __device__ __noinline__ void feynman_value(const double *xin, int d, cons
     }
     if (F.im > 0.0) ++signfail;
     // J_kl = delta_kl - i lam [delta_kl (1 - 2 x_k) dF_k + x_k (1 - x_k) d2F_kl]
-    const cplx det = feynman_jacobian_det(x, xo, grad, H, d, lam);
+    const cplx det = feynman_jacobian_det<0>(x, xo, grad, H, d, lam);
     feynman_combine(U, F, det, ps.pa, ps.pb, re, im);
 }
 

@@ -288,7 +288,8 @@ void qmc_batch_plan_destroy(qmc_batch_plan *plan);
 
 /* Chooses the launch shape for a batch by timing candidate configurations
  * (streams_per_block in {256/m, 128/m, 64/m} x points_per_stream in {16..512}) on a sample
- * of at most 256 items (CUDA events on `stream`).  workspace and sums as for
+ * of at most 256 items, each cut to the first max(2^16, 2^23 / items) points of its range
+ * so that a candidate costs a bounded time (CUDA events on `stream`).  workspace and sums as for
  * qmc_batch_sums of the same items (the sample needs no more).  best receives the fastest
  * configuration.  Overwrites sums. */
 int qmc_batch_autotune(const qmc_batch_item *items, int count, void *workspace,
@@ -419,6 +420,22 @@ int qmc_merge_sums(const double *parts, uint64_t nparts, uint64_t len, double *o
 size_t qmc_cbc_device_bytes(uint64_t n);
 int qmc_cbc_korobov(uint64_t n, int s, double gamma, double beta, uint64_t *z_out,
                     double *e2_out, void *stream);
+
+/* ---- measurement: unit throughput probes ------------------------------------------- */
+
+/* The paper has no counterpart: these measure the two arithmetic units the lattice sums
+ * run on, for the roofline of qmc_sums on the device at hand.  QMC_PROBE_FP64_FMA runs
+ * chains of FP64 fused multiply-adds; QMC_PROBE_INT_MULHI runs chains of the truncated
+ * 64-bit high product the kernel's fixed-point transforms and Genz forms use (one
+ * 32 x 32 -> 64-bit multiply and two 32-bit high multiplies).  One launch of
+ * SMs x (resident blocks per SM) blocks of 256 threads, each thread running trips x 32
+ * operations on 8 independent chains; *ops_out (host) receives the operations launched
+ * (FMAs, or 32-bit multiplies).  sink: device, one double (written only in a case that
+ * does not occur; it keeps the chains live).  The call only enqueues: time it with events
+ * on `stream`.  Errors: QMC_ERR_ARG (unknown unit, NULL, trips < 1), QMC_ERR_NO_DEVICE,
+ * QMC_ERR_CUDA. */
+enum { QMC_PROBE_FP64_FMA = 1, QMC_PROBE_INT_MULHI = 2 };
+int qmc_probe_units(int unit, uint32_t trips, double *sink, double *ops_out, void *stream);
 
 /* ---- host entry points -------------------------------------------------------------- */
 

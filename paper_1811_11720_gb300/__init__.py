@@ -26,7 +26,7 @@ from ._capi import (FAMILY, QMC_MAX_DIM, STATUS, TRANSFORM, qmc_batch_config, qm
 __all__ = ["QMCError", "lib", "GenvecTable", "Integrand", "make_transform", "get_next_n",
            "make_shifts", "rule", "points", "sums_workspace_bytes", "sums", "sums_noalloc",
            "sums_tile_count", "sums_tiles", "reduce_tiles",
-           "finalize",
+           "finalize", "probe_units",
            "evaluate", "histogram_workspace_bytes", "histogram", "fit_polysingular",
            "integrate", "integrate_device", "Batch", "Server", "cbc_korobov", "DEFAULT_TABLE",
            "EXTENSION_TABLE"]
@@ -304,6 +304,18 @@ def sums_noalloc(f: qmc_integrand, r: qmc_rule, i_begin: int, i_end: int, out, c
     _check(lib().qmc_sums_noalloc(C.byref(f), C.byref(r), int(i_begin), int(i_end), _ptr(out),
                                   _ptr(counters), _stream(stream)), "sums_noalloc")
     return out
+
+
+PROBE_UNITS = {"fp64_fma": 1, "int_mulhi": 2}
+
+
+def probe_units(unit: str, trips: int, sink, stream=None) -> float:
+    """qmc_probe_units: enqueue one throughput probe of ``unit`` ("fp64_fma" or "int_mulhi")
+    and return the operations it executes (time it with events on ``stream``)."""
+    ops = C.c_double()
+    _check(lib().qmc_probe_units(PROBE_UNITS[unit], int(trips), _ptr(sink), C.byref(ops),
+                                 _stream(stream)), "probe_units")
+    return float(ops.value)
 
 
 def finalize(sums_dev, m: int, n: int, is_complex: bool, result, Q=None, stream=None):

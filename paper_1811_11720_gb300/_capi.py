@@ -130,6 +130,7 @@ PROTOTYPES = {
     "qmc_reduce_tiles": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int, C.c_void_p,
                                    C.c_void_p]),
     "qmc_merge_sums": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p]),
+    "qmc_probe_units": (C.c_int, [C.c_int, C.c_uint32, C.c_void_p, _P(C.c_double), C.c_void_p]),
     "qmc_cbc_device_bytes": (C.c_size_t, [C.c_uint64]),
     "qmc_cbc_korobov": (C.c_int, [C.c_uint64, C.c_int, C.c_double, C.c_double, _P(C.c_uint64),
                                   _P(C.c_double), C.c_void_p]),

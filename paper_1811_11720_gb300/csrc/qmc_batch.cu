@@ -344,6 +344,11 @@ extern "C" int qmc_batch_autotune(const qmc_batch_item *items, int count, void *
     const int step = std::max(1, count / 256);
     std::vector<qmc_batch_item> sample;
     for (int q = 0; q < count; q += step) sample.push_back(items[q]);
+    // bounded cost per candidate: at most ~2^23 points in all, each item's range cut to its
+    // share from its start (the candidates are compared on the same work)
+    const uint64_t share = std::max<uint64_t>(1u << 16, (1u << 23) / sample.size());
+    for (auto &it : sample)
+        if (it.i_end > it.i_begin + share) it.i_end = it.i_begin + share;
     const int m = (int)items[0].rule.m;
     if (m < 1 || m > kMaxShiftGroup) return QMC_ERR_M;
     const int spb_max = std::max(1, kSumsThreads / m);

@@ -1,9 +1,11 @@
 """The benchmark's workload definition and its FP64 work count, on the CPU: the 45 Genz
 integrals (families 1, 3, 4 x d = 6, 8, 10 x baker and Korobov-1..4) with seeded
 parameters in the paper's difficulty ranges (Sec. 5.2), the single-integral selection used
-for profiling, and the per-evaluation FP64 count behind the roofline's `achieved` (the
+for profiling, the per-evaluation FP64 count behind the roofline's `fp64_equivalent` (the
 method's FP64 work: Korobov-r costs (2r+1) fma + (r+2) mul + 1 mul per dimension, baker 2,
-the family's form and its final function, and the weighted accumulation)."""
+the point's add and compare per dimension, the family's form and its final function, and
+the weighted accumulation), and the integer-multiply count behind its `achieved` (the
+fixed-point form's 32-bit multiplies, restated here from the primitives' definitions)."""
 from __future__ import annotations
 
 import pytest
@@ -40,9 +42,9 @@ def test_only_selects_one_integral():
 
 
 @pytest.mark.parametrize("fam,tr,d,expect", [
-    (4, ("korobov", 3), 10, 10 * (2 * 7 + 5 + 1) + 3 * 10 + 1 + 2),
-    (1, ("baker",), 6, 2 * 6 + 2 * 6 + 1 + 2),
-    (3, ("korobov", 1), 8, 8 * (2 * 3 + 3 + 1) + 2 * 8 + 4 + 1 + 2),
+    (4, ("korobov", 3), 10, 10 * (2 * 7 + 5 + 1) + 3 * 10 + 1 + 2 + 2 * 10),
+    (1, ("baker",), 6, 2 * 6 + 2 * 6 + 1 + 2 + 2 * 6),
+    (3, ("korobov", 1), 8, 8 * (2 * 3 + 3 + 1) + 2 * 8 + 4 + 1 + 2 + 2 * 8),
 ])
 def test_fp64_work_count(fam, tr, d, expect):
     assert bench.fp64_flops_per_eval(fam, tr, d) == expect
@@ -54,3 +56,38 @@ def test_feynman_workload_shape():
     for fam, d, tr, fl, _ in items:
         assert fam == bench.FEYNMAN_FAMILY and d == 5 and tr == ("korobov", 3)
         assert bench.feynman_flops_per_eval(fl) > 500
+
+
+# 32-bit multiplies of the fixed-point primitives: a truncated 64-bit high product takes
+# three (32x32->64 of the high halves, two 32-bit high cross products), its square two.
+@pytest.mark.parametrize("r,expect", [
+    # v^2 (2) + P(w): r=1 none, r=2,3 one product (3), r=4 product + square + product (8)
+    # + v^(r+1): r=1 none (v^2), r=2 v^2 v (3), r=3 (v^2)^2 (2), r=4 (v^2)^2 v (5)
+    # + phi = v^(r+1) P (3) + the weight factor into the running product (3)
+    (1, 2 + 0 + 0 + 3 + 3), (2, 2 + 3 + 3 + 3 + 3), (3, 2 + 3 + 2 + 3 + 3),
+    (4, 2 + 8 + 5 + 3 + 3)])
+def test_korobov_map_multiplies(r, expect):
+    assert bench.korobov_map_muls(r) == expect
+
+
+@pytest.mark.parametrize("fam,tr,d,expect", [
+    # Gaussian, Korobov-3, d = 10: map 13 + form (product 3 + square 2) per dimension,
+    # weight^3 (square 2 + product 3) times C^d (3), integer exp (Tang: 31)
+    (4, ("korobov", 3), 10, 10 * (13 + 5) + (2 + 3 + 3) + 31),
+    # Gaussian, Korobov-4: the exp is in FP64 above r = 3
+    (4, ("korobov", 4), 10, 10 * (21 + 5) + (2 + 2 + 3)),
+    # oscillatory, baker, d = 6: one product per dimension and the cos in turns (29)
+    (1, ("baker",), 6, 6 * 3 + 29),
+    # corner peak, Korobov-1, d = 8: the 9th power (3 squares, 1 product) and reciprocal (22)
+    (3, ("korobov", 1), 8, 8 * (8 + 3) + 3 + (3 * 2 + 3) + 22),
+    # corner peak, Korobov-2: FP64 power and division above r = 1
+    (3, ("korobov", 2), 8, 8 * (14 + 3) + (2 + 3)),
+])
+def test_int_multiply_work_count(fam, tr, d, expect):
+    assert bench.int_mul_per_eval(fam, tr, d) == expect
+
+
+def test_int_multiply_work_is_positive_for_the_benchmark():
+    for fam, d, tr, c, _ in bench.workload_items():
+        assert bench.int_mul_per_eval(fam, tr, d, c) > 0
+

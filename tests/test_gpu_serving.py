@@ -209,3 +209,40 @@ def test_server_rejects_bad_arguments(env):
     with pytest.raises(q.QMCError):
         srv.submit(q.Integrand.trig(np.array([0.5]), np.array([1]), np.array([0.1])), epsrel=1e-3)
     srv.close()
+
+
+def test_served_results_match_the_oracle_on_their_final_lattice(env):
+    """Each served request ends on one lattice of the table (Sec. 3.3.1: results of the
+    smaller lattices are discarded on escalation).  For real Genz and complex deformed
+    requests served together, the final (Qbar, sigma) must equal the oracle's estimate on
+    that lattice with the request's shifts (SplitMix64 seeded with its seed): Qbar within
+    1e-12 of the mean |g| per component, sigma within max(1e-9 sigma, 2e-12 mean |g|)."""
+    import oracle as O
+    q, torch, tab = env
+    m = 16
+    reqs = []
+    for i, (fam, d) in enumerate([(4, 5), (2, 4), (1, 6), (3, 3)]):
+        c, w = W.genz_params(fam, d, 60 + i)
+        reqs.append((q.Integrand.genz(fam, c, w), O.genz(fam, c, w), 10.0 ** -(4 + i % 3)))
+    for i in range(3):
+        fl = W.feynman_regular(70 + i, beta=0.6 if i % 2 == 0 else 0.95, lam=1.0)
+        reqs.append((q.Integrand.polynomial(fl), O.feynman_complex(fl), 10.0 ** -(2 + i)))
+    srv = q.Server(tab, memory_budget=256 << 20, max_slots=16, m=m)
+    ids = [srv.submit(f, epsrel=eps, epsabs=0.0, minn=1021, maxeval=3_000_000, seed=80 + i)
+           for i, (f, _, eps) in enumerate(reqs)]
+    _drain(srv, ids, max_steps=400)
+    got = [srv.status(i) for i in ids]
+    srv.close()
+    for i, ((f, of, eps), g) in enumerate(zip(reqs, got)):
+        n = int(g["n"])
+        assert n in tab and int(g["m"]) == m
+        D = O.shifts(80 + i, m, f.dim)
+        o = O.integrate(of, ("korobov", 3), n, tab.z_for(n)[:f.dim], D)
+        A = o["A"].mean()
+        assert abs(g["integral"].real - o["value_re"]) <= 1e-12 * A, (i, n)
+        assert abs(g["error"].real - o["error_re"]) <= max(1e-9 * o["error_re"], 2e-12 * A), (i, n)
+        if f.is_complex:
+            assert abs(g["integral"].imag - o["value_im"]) <= 1e-12 * A, (i, n)
+            assert abs(g["error"].imag - o["error_im"]) <= max(1e-9 * o["error_im"], 2e-12 * A), (i, n)
+        else:
+            assert g["integral"].imag == 0.0

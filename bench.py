@@ -54,8 +54,12 @@ M_SHIFTS = 32
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) of one lattice-sum launch from an ncu capture of the current
-# kernel, or None when the kernel has changed since the capture.
-TRAFFIC_BYTES_PER_LAUNCH = None
+# kernel, or None when the kernel has changed since the capture: sums_kernel<Gaussian,
+# integer Korobov>, d = 10, Korobov-3, n = 1,072,187, m = 32 (2272 tiles): 92,672 bytes
+# read, 0 written (the partials stay in L2).  The inputs are kilobytes and the partials
+# grow only with the tile count (at most six waves of 760), so the figure stands for the
+# benchmark's launches.
+TRAFFIC_BYTES_PER_LAUNCH = 92_672
 
 # 32-bit integer multiplies of the fixed-point primitives (qmc_fixed.cuh):
 MUL_HI = 3        # truncated 64-bit high product: one 32x32->64, two 32-bit high multiplies
@@ -953,6 +957,11 @@ def run_extras(args) -> dict:
                                   serve_profile="feynman", serve_maxeval=EXTRA_SERVE_MAXEVAL))
         return r
 
+    def serve_small():
+        # launch-bound requests: 512 small d = 4 Genz integrals at 16,000 arrivals/s
+        return run_serve_workload(ns(requests=64, rates=[16000.0], serve_profile="small",
+                                     serve_maxeval=3.2e7))
+
     def small_lattice():
         # the 45 Genz integrals on the table size just above 1e5 (launch-bound regime):
         # the step as the main line runs it, and the same step replayed from a CUDA graph
@@ -974,6 +983,7 @@ def run_extras(args) -> dict:
     guarded("feynman", feynman)
     guarded("batch", batch)
     guarded("serve", serve)
+    guarded("serve_small", serve_small)
     return out
 
 

@@ -21,7 +21,7 @@ __device__ __forceinline__ void batch_stream(const BatchItem &it, const FamilySh
                                              int q, double &acc_re, double &acc_im,
                                              unsigned long long &nonfinite,
                                              unsigned long long &signfail) {
-    stream_sums<FAM, TK>(it, fsh, s_fit, it.fit != nullptr, dsh, it.cd, i0, cnt, wl, q, acc_re,
+    stream_sums<FAM, TK>(it, fsh, s_fit, it.fit != nullptr, ShiftsPre{dsh}, it.cd, i0, cnt, wl, q, acc_re,
                          acc_im, nonfinite, signfail);
 }
 

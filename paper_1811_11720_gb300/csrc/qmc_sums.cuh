@@ -73,11 +73,22 @@ __device__ __forceinline__ int lattice_group_lanes(int m, int d) {
     return 0;
 }
 
+// Shift accessors: dsh(j) is D_kj 2^11, the thread's 53-bit shift of coordinate j in units
+// of the lattice state's top word.
+struct ShiftsPre {      // values already multiplied by 2^11 (local or shared memory)
+    const uint64_t *s;
+    __device__ __forceinline__ uint64_t operator()(int j) const { return s[j]; }
+};
+struct ShiftsGlobal {   // the caller's row of D_kj in global memory, through the read-only path
+    const uint64_t *D;
+    __device__ __forceinline__ uint64_t operator()(int j) const { return __ldg(D + j) << 11; }
+};
+
 // One evaluation of g at the point whose coordinate j has lattice state (fhi(j), flo(j),
 // rem(j)); adds it to the two-level accumulator.
-template <int FAM, int TK, int R, class P, class Hi, class Lo, class Rem>
+template <int FAM, int TK, int R, class P, class Sh, class Hi, class Lo, class Rem>
 __device__ __forceinline__ void eval_point(const P &p, const FamilyShared &fsh, const double *s_fit,
-                                           bool use_fit, const uint64_t *dsh, double cd, Hi fhi,
+                                           bool use_fit, Sh dsh, double cd, Hi fhi,
                                            Lo flo, Rem rem, double &g_re, double &g_im,
                                            unsigned long long &signfail) {
     Weight W{1.0, 1.0, 1.0, Fx{0x8000000000000000ull, 1}};
@@ -94,7 +105,7 @@ __device__ __forceinline__ void eval_point(const P &p, const FamilyShared &fsh, 
             fa.init_fixed();
 #pragma unroll 1
             for (int j = 0; j < p.d; ++j)
-                fa.template add_fixed<kIntFinish>(j, transform_fixed<TK, R>(fhi(j) + dsh[j], W), fsh);
+                fa.template add_fixed<kIntFinish>(j, transform_fixed<TK, R>(fhi(j) + dsh(j), W), fsh);
             const double wt = weight_finish<TK, R>(W, p.t, cd);
             fa.template finish_fixed<kIntFinish>(p.d, fsh, g_re, g_im, signfail);
             g_re *= wt;
@@ -106,9 +117,9 @@ __device__ __forceinline__ void eval_point(const P &p, const FamilyShared &fsh, 
     for (int j = 0; j < p.d; ++j) {
         Mapped mx;
         if constexpr (TK == kTKorobovInt) {
-            mx = korobov_int_x<R>(fhi(j) + dsh[j], W);
+            mx = korobov_int_x<R>(fhi(j) + dsh(j), W);
         } else {
-            const double u = fixed_to_double(fhi(j) + dsh[j], flo(j), rem(j), p.n);
+            const double u = fixed_to_double(fhi(j) + dsh(j), flo(j), rem(j), p.n);
             mx = apply_transform<TK>(u, p.t, W);
         }
         if (use_fit) mx = Mapped{apply_fit(reflected(mx), s_fit + kFitStride * j, W.w), false};
@@ -132,9 +143,9 @@ __device__ __forceinline__ void eval_point(const P &p, const FamilyShared &fsh, 
 // (broadcast loads), with one __syncwarp over the group per point.  That is one lattice
 // step per lane and point instead of d.  Otherwise each thread keeps all d coordinates in
 // local memory (L1) and steps them itself.
-template <int FAM, int TK, int R, class P>
+template <int FAM, int TK, int R, class P, class Sh>
 __device__ __forceinline__ void stream_sums_r(const P &p, const FamilyShared &fsh, const double *s_fit,
-                                              bool use_fit, const uint64_t *dsh, double cd,
+                                              bool use_fit, Sh dsh, double cd,
                                               uint64_t i0, uint64_t cnt, WarpLattice *wl,
                                               int q, double &acc_re, double &acc_im,
                                               unsigned long long &nonfinite,
@@ -230,9 +241,9 @@ __device__ __forceinline__ void stream_sums_r(const P &p, const FamilyShared &fs
 }
 
 // The integer Korobov is compiled once per order r (uniform branch per stream).
-template <int FAM, int TK, class P>
+template <int FAM, int TK, class P, class Sh>
 __device__ __forceinline__ void stream_sums(const P &p, const FamilyShared &fsh, const double *s_fit,
-                                            bool use_fit, const uint64_t *dsh, double cd,
+                                            bool use_fit, Sh dsh, double cd,
                                             uint64_t i0, uint64_t cnt, WarpLattice *wl, int q,
                                             double &acc_re, double &acc_im,
                                             unsigned long long &nonfinite,
@@ -326,50 +337,45 @@ __global__ void __launch_bounds__(kSumsThreads, kSumsMinBlocks<FAM>)
     double cd = 1.0;  // Korobov C^d
     if constexpr (TK == QMC_T_KOROBOV || TK == kTKorobovInt) cd = ipow_u(p.t.C, d);
 
-    // The shifts D_kj 2^11 (the 53-bit shift in the high word's units), read once per
-    // dimension of every evaluation, are per-thread values in local memory, which misses
-    // L1 (the shared memory of five blocks leaves little of it).  Under the cheap maps
-    // (baker, none) the separable families stage them in shared memory instead, in the
-    // polynomial buffer they do not use, as [k][j] rows of odd length (the warp's lanes hit
-    // distinct banks): +2 to +10 % there, while under the integer Korobov map the
-    // generic loads this needs cost more than the misses.
-    uint64_t dsh_local[kMaxDim];
-    const uint64_t *dsh = dsh_local;
+    // The shifts D_kj, read once per dimension of every evaluation.  Under the cheap maps
+    // (baker, none) the separable families stage them, times 2^11 (the 53-bit shift in the
+    // high word's units), in shared memory, in the polynomial buffer they do not use, as
+    // [k][j] rows of odd length (the warp's lanes hit distinct banks).  Otherwise each
+    // thread reads its row of the caller's array through the read-only cache: the block's
+    // m rows (m d 8 bytes) are shared by all its warps and stay in L1, where a copy per
+    // thread in local memory (spb times as much) missed.
+    unsigned long long nonfinite = 0, signfail = 0;
+    const uint64_t ptile = (uint64_t)p.spb * p.L;
+    const int q = lattice_group_lanes(m, d);
+    auto run_tiles = [&](auto dsh) {
+        for (uint64_t tile = blockIdx.x; tile < p.tiles; tile += gridDim.x) {
+            const uint64_t i0 = p.i_begin + tile * ptile + (uint64_t)s_local * p.L;
+            uint64_t cnt = 0;
+            if (active && i0 < p.i_end) cnt = (p.i_end - i0 < p.L) ? (p.i_end - i0) : p.L;
+            double acc_re, acc_im;
+            stream_sums<FAM, TK>(p, fsh, s_fit, p.fit != nullptr, dsh, cd, i0, cnt,
+                                 q ? &s_lat[tid >> 5] : nullptr, q, acc_re, acc_im, nonfinite,
+                                 signfail);
+            double *out_re = p.partials + 2 * (tile * (uint64_t)m);
+            double *out_im = p.partials + 2 * (p.tiles * (uint64_t)m) + 2 * (tile * (uint64_t)m);
+            tile_partial<kCplx>(acc_re, acc_im, s_red, m, p.spb, s_local, k, active, out_re, out_im);
+        }
+    };
     bool staged = false;
     if constexpr (!kPolyFamily<FAM> && (TK == QMC_T_BAKER || TK == QMC_T_NONE)) {
         const int ds = d | 1;
-        if (m * ds <= 4 * kMaxTerms) {
+        if (m * ds <= 4 * kMaxTerms) {   // uniform over the block
             uint64_t *s_dsh = fsh.poly.buf.u;
             for (int i = tid; i < m * ds; i += blockDim.x) {
                 const int kk = i / ds, j = i - kk * ds;
                 s_dsh[i] = j < d ? (p.shifts[(size_t)kk * d + j] << 11) : 0ull;
             }
-            dsh = s_dsh + k * ds;
-            staged = true;
             __syncthreads();
+            run_tiles(ShiftsPre{s_dsh + k * ds});
+            staged = true;
         }
     }
-    if (!staged) {
-#pragma unroll 1
-        for (int j = 0; j < d; ++j) dsh_local[j] = active ? (p.shifts[(size_t)k * d + j] << 11) : 0ull;
-    }
-
-    unsigned long long nonfinite = 0, signfail = 0;
-    const uint64_t ptile = (uint64_t)p.spb * p.L;
-
-    for (uint64_t tile = blockIdx.x; tile < p.tiles; tile += gridDim.x) {
-        const uint64_t i0 = p.i_begin + tile * ptile + (uint64_t)s_local * p.L;
-        uint64_t cnt = 0;
-        if (active && i0 < p.i_end) cnt = (p.i_end - i0 < p.L) ? (p.i_end - i0) : p.L;
-        double acc_re, acc_im;
-        const int q = lattice_group_lanes(m, d);
-        stream_sums<FAM, TK>(p, fsh, s_fit, p.fit != nullptr, dsh, cd, i0, cnt,
-                             q ? &s_lat[tid >> 5] : nullptr, q, acc_re, acc_im, nonfinite,
-                             signfail);
-        double *out_re = p.partials + 2 * (tile * (uint64_t)m);
-        double *out_im = p.partials + 2 * (p.tiles * (uint64_t)m) + 2 * (tile * (uint64_t)m);
-        tile_partial<kCplx>(acc_re, acc_im, s_red, m, p.spb, s_local, k, active, out_re, out_im);
-    }
+    if (!staged) run_tiles(ShiftsGlobal{p.shifts + (size_t)k * d});
     if (p.counters && (nonfinite | signfail)) {
         if (nonfinite) atomicAdd(p.counters, nonfinite);
         if (signfail) atomicAdd(p.counters + 1, signfail);

@@ -1014,6 +1014,9 @@ def main():
                     help="server step budget in evaluations (0: all running requests each step)")
     ap.add_argument("--batch-count", type=int, default=2000)
     ap.add_argument("--batch-nmax", type=float, default=1e8)
+    ap.add_argument("--graph", action="store_true",
+                    help="replay each timed step from a CUDA graph (host launch work out of "
+                         "the timed region; no per-launch kernel events)")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="skip the bounded latency/feynman/batch/serve runs after the main line")
     args = ap.parse_args()

@@ -155,8 +155,30 @@ __device__ __forceinline__ void stage_fixed_forms(const P &p, FixedForms &fx) {
     }
 }
 
-// P: SumsParams or BatchItem (fields d, c, w, h, nu, nf, ucoef, fcoef, uexp, fexp, pa, pb, lam)
+// Subset sums of c over the reflected dimensions, for the FP64 forms of families 1, 3
+// and 6 (reflected_c_sum); the fixed-point forms do not read them.
 template <int FAM, class P>
+__device__ __forceinline__ void stage_subset_sums(const P &p, FamilyShared &fs) {
+    if constexpr (FAM == QMC_GENZ_OSCILLATORY || FAM == QMC_GENZ_CORNER_PEAK ||
+                  FAM == QMC_GENZ_DISCONTINUOUS) {
+        for (int b = threadIdx.x; b < 256; b += blockDim.x) {
+            double lo = 0.0, hi = 0.0;
+            for (int j = 0; j < 8; ++j) {
+                if ((b >> j) & 1) {
+                    if (j < p.d) lo += p.c[j];
+                    if (j + 8 < p.d) hi += p.c[j + 8];
+                }
+            }
+            fs.sub_lo[b] = lo;
+            fs.sub_hi[b] = hi;
+        }
+    }
+}
+
+// P: SumsParams or BatchItem (fields d, c, w, h, nu, nf, ucoef, fcoef, uexp, fexp, pa, pb, lam).
+// kSubsets = false leaves the subset-sum tables to the caller (stage_subset_sums), which
+// builds them only when an FP64 form may run.
+template <int FAM, bool kSubsets = true, class P>
 __device__ __forceinline__ void stage_family(const P &p, FamilyShared &fs) {
     const int tid = threadIdx.x;
     if constexpr (FAM == QMC_SECTOR || FAM == QMC_FEYNMAN) {
@@ -174,20 +196,7 @@ __device__ __forceinline__ void stage_family(const P &p, FamilyShared &fs) {
             fs.h[tid] = p.h ? p.h[tid] : 0;
         }
         if (tid == 0) fs.s0 = (FAM == QMC_GENZ_OSCILLATORY && p.w) ? 6.283185307179586476925 * p.w[0] : 0.0;
-        if constexpr (FAM == QMC_GENZ_OSCILLATORY || FAM == QMC_GENZ_CORNER_PEAK ||
-                      FAM == QMC_GENZ_DISCONTINUOUS) {
-            for (int b = tid; b < 256; b += blockDim.x) {
-                double lo = 0.0, hi = 0.0;
-                for (int j = 0; j < 8; ++j) {
-                    if ((b >> j) & 1) {
-                        if (j < p.d) lo += p.c[j];
-                        if (j + 8 < p.d) hi += p.c[j + 8];
-                    }
-                }
-                fs.sub_lo[b] = lo;
-                fs.sub_hi[b] = hi;
-            }
-        }
+        if constexpr (kSubsets) stage_subset_sums<FAM>(p, fs);
         if constexpr (kHasFixedForm<FAM>) stage_fixed_forms<FAM>(p, fs.fx);
         if constexpr (FAM == QMC_GENZ_OSCILLATORY) {
             for (int i = tid; i < 65; i += blockDim.x) fs.cos256[i] = kCos256[i];

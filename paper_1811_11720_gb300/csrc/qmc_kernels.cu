@@ -104,32 +104,41 @@ cudaError_t launch_reduce_tiles(const double *partials, uint64_t tiles, int m, i
 }
 
 // Eq. (lattice) and Eq. (lattice-error): Q_k = S_k / n, Qbar, sigma, per component.
-// One thread, the summation order fixed (k = 0..m-1) and shared with the batched form;
-// the restrict qualifiers let the loads and divisions of different k overlap.
-__global__ void finalize_kernel(const double *__restrict__ sums, int m, uint64_t n, int is_complex,
-                                double *__restrict__ result, double *__restrict__ Q) {
-    if (threadIdx.x != 0) return;
+// The m divisions run in parallel (one thread per shift and component); the mean and the
+// variance are then summed by one thread per component in fixed order k = 0..m-1, the
+// order the batched form uses, so both give the same bits.
+constexpr int kFinThreads = 256;
+
+__global__ void __launch_bounds__(kFinThreads)
+    finalize_kernel(const double *__restrict__ sums, int m, uint64_t n, int is_complex,
+                    double *__restrict__ result, double *__restrict__ Q) {
+    __shared__ double q_s[2 * QMC_MAX_SHIFTS];
     const double dn = (double)n;
-    for (int comp = 0; comp < (is_complex ? 2 : 1); ++comp) {
-        const double *__restrict__ sc = sums + 2 * (size_t)comp * m;
-        double mean = 0.0;
-#pragma unroll 8
-        for (int k = 0; k < m; ++k) {
-            double q = (sc[2 * k] + sc[2 * k + 1]) / dn;
-            if (Q) Q[(size_t)comp * m + k] = q;
-            mean += q;
-        }
-        mean /= (double)m;
-        double var = 0.0;
-#pragma unroll 8
-        for (int k = 0; k < m; ++k) {
-            double q = (sc[2 * k] + sc[2 * k + 1]) / dn - mean;
-            var = fma(q, q, var);
-        }
-        var /= (double)m * (double)(m - 1);
-        result[2 * comp] = mean;
-        result[2 * comp + 1] = sqrt(var);
+    const int ncomp = is_complex ? 2 : 1;
+    for (int i = threadIdx.x; i < ncomp * m; i += blockDim.x) {
+        const int comp = i / m, k = i - comp * m;
+        const double *sc = sums + 2 * (size_t)comp * m;
+        const double q = (sc[2 * k] + sc[2 * k + 1]) / dn;
+        q_s[i] = q;
+        if (Q) Q[i] = q;
     }
+    __syncthreads();
+    const int comp = threadIdx.x;
+    if (comp >= ncomp) return;
+    const double *qc = q_s + (size_t)comp * m;
+    double mean = 0.0;
+#pragma unroll 8
+    for (int k = 0; k < m; ++k) mean += qc[k];
+    mean /= (double)m;
+    double var = 0.0;
+#pragma unroll 8
+    for (int k = 0; k < m; ++k) {
+        const double dq = qc[k] - mean;
+        var = fma(dq, dq, var);
+    }
+    var /= (double)m * (double)(m - 1);
+    result[2 * comp] = mean;
+    result[2 * comp + 1] = sqrt(var);
     if (!is_complex) {
         result[2] = 0.0;
         result[3] = 0.0;
@@ -138,7 +147,9 @@ __global__ void finalize_kernel(const double *__restrict__ sums, int m, uint64_t
 
 cudaError_t launch_finalize(const double *sums, int m, uint64_t n, int is_complex,
                             double *result, double *Q, cudaStream_t s) {
-    finalize_kernel<<<1, 32, 0, s>>>(sums, m, n, is_complex, result, Q);
+    const int work = m * (is_complex ? 2 : 1);
+    const int threads = work >= kFinThreads ? kFinThreads : ((work + 31) / 32) * 32;
+    finalize_kernel<<<1, threads, 0, s>>>(sums, m, n, is_complex, result, Q);
     return cudaGetLastError();
 }
 

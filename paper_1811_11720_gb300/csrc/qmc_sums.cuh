@@ -326,9 +326,17 @@ __global__ void __launch_bounds__(kSumsThreads, kSumsMinBlocks<FAM>)
     constexpr bool kCplx = FamilyAcc<FAM>::kComplex;
 
     const int tid = threadIdx.x;
-    stage_family<FAM>(p, fsh);
+    stage_family<FAM, false>(p, fsh);
     prepare_fit(p.fit, p.d, s_fit);
     __syncthreads();
+    if constexpr (kHasFixedForm<FAM>) {
+        // the FP64 forms' subset-sum tables (256 FP64 sums per block), only when the
+        // fixed-point form does not take every evaluation (uniform over the block)
+        if (!(kFixedTransform<TK> && p.fit == nullptr && fsh.fx.ok)) {
+            stage_subset_sums<FAM>(p, fsh);
+            __syncthreads();
+        }
+    }
 
     const int m = p.m, d = p.d;
     const int k = tid % m;

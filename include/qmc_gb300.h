@@ -173,7 +173,10 @@ int qmc_make_shifts(uint64_t seed, uint64_t m, int dim, uint64_t *D_out);
 int qmc_points(const qmc_rule *rule, uint64_t i_begin, uint64_t count, double *out, void *stream);
 
 /* Device scratch needed by qmc_sums for the i-range [i_begin, i_end) (per-tile partial
- * sums; the tiling is fixed by the range, not by the device). */
+ * sums; the tiling is fixed by the range, not by the device).  For m <= 256 a qmc_sums
+ * call leaves its tile partials at the start of the workspace in the layout of
+ * qmc_sums_tiles (tiles x m (sum, compensation) pairs, then the imaginary block), so a
+ * caller can check or reuse them. */
 size_t qmc_sums_workspace_bytes(const qmc_rule *rule, int is_complex, uint64_t i_begin,
                                 uint64_t i_end);
 

@@ -131,20 +131,6 @@ cudaError_t launch_batch_finalize(const BatchItem *d_items, int count, int m, in
     return cudaGetLastError();
 }
 
-// C^d by the same left-to-right binary powering as the device code (ipow_u), so a batch
-// with the default launch shape reproduces qmc_sums bit for bit.
-double ipow_host(double x, int e) {
-    if (e <= 0) return 1.0;
-    int top = 31;
-    while (!((e >> top) & 1)) --top;
-    double r = x;
-    for (int b = top - 1; b >= 0; --b) {
-        r *= r;
-        if ((e >> b) & 1) r *= x;
-    }
-    return r;
-}
-
 int fill_batch_item(BatchItem &it, const qmc_batch_item &b, int m, int spb, uint32_t Lcfg, int fam) {
     int st = check_integrand_shape(&b.f);
     if (st) return st;
@@ -169,7 +155,7 @@ int fill_batch_item(BatchItem &it, const qmc_batch_item &b, int m, int spb, uint
     for (int j = 0; j < it.d; ++j) it.dc[j] = dim_const(b.rule.z[j] % b.rule.n, b.rule.n);
     it.shifts = b.rule.shifts;
     it.t = make_transform(b.rule.transform);
-    it.cd = (b.rule.transform.kind == QMC_T_KOROBOV) ? ipow_host(it.t.C, it.d) : 1.0;
+    it.cd = korobov_cd(b.rule.transform, it.t, it.d);
     it.fit = b.rule.fit;
     it.family = fam;
     it.c = b.f.c;

@@ -132,6 +132,7 @@ int qmc_sums(const qmc_integrand *f, const qmc_rule *rule, uint64_t i_begin, uin
     p.d = rule->dim;
     for (int j = 0; j < rule->dim; ++j) p.dc[j] = dim_const(rule->z[j] % rule->n, rule->n);
     p.t = make_transform(rule->transform);
+    p.cd = korobov_cd(rule->transform, p.t, rule->dim);
     p.fit = rule->fit;
     fill_integrand(p, f);
     p.counters = counters;
@@ -203,6 +204,7 @@ int qmc_sums_tiles(const qmc_integrand *f, const qmc_rule *rule, uint64_t i_begi
     p.d = rule->dim;
     for (int j = 0; j < rule->dim; ++j) p.dc[j] = dim_const(rule->z[j] % rule->n, rule->n);
     p.t = make_transform(rule->transform);
+    p.cd = korobov_cd(rule->transform, p.t, rule->dim);
     p.fit = rule->fit;
     fill_integrand(p, f);
     p.counters = counters;

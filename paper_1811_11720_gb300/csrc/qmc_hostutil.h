@@ -92,6 +92,23 @@ inline TransformParams make_transform(const qmc_transform &t) {
     return tp;
 }
 
+// C^d of the Korobov weight (1 for the other transforms) by left-to-right binary powering:
+// computed once per launch on the host, the same value for qmc_sums and batches.
+inline double ipow_host(double x, int e) {
+    if (e <= 0) return 1.0;
+    int top = 31;
+    while (!((e >> top) & 1)) --top;
+    double r = x;
+    for (int b = top - 1; b >= 0; --b) {
+        r *= r;
+        if ((e >> b) & 1) r *= x;
+    }
+    return r;
+}
+inline double korobov_cd(const qmc_transform &t, const TransformParams &tp, int d) {
+    return t.kind == QMC_T_KOROBOV ? ipow_host(tp.C, d) : 1.0;
+}
+
 inline bool is_complex_family(int fam) { return fam == QMC_FEYNMAN; }
 
 inline bool family_known(int fam) {

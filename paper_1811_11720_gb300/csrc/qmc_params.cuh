@@ -38,6 +38,7 @@ struct SumsParams {
     DimConst dc[kMaxDim];
     const uint64_t *shifts;   // [m][d]
     TransformParams t;
+    double cd;                // Korobov C^d, 1 for the other transforms
     const double *fit;        // [d][6] or nullptr
     // integrand (device pointers; the kernel stages them in shared memory)
     int family;

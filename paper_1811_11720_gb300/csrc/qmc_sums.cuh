@@ -342,8 +342,7 @@ __global__ void __launch_bounds__(kSumsThreads, kSumsMinBlocks<FAM>)
     const int k = tid % m;
     const int s_local = tid / m;
     const bool active = s_local < p.spb;
-    double cd = 1.0;  // Korobov C^d
-    if constexpr (TK == QMC_T_KOROBOV || TK == kTKorobovInt) cd = ipow_u(p.t.C, d);
+    const double cd = p.cd;   // Korobov C^d (host-computed; 1 otherwise)
 
     // The shifts D_kj, read once per dimension of every evaluation.  Under the cheap maps
     // (baker, none) the separable families stage them, times 2^11 (the 53-bit shift in the

@@ -152,3 +152,81 @@ def test_whole_lattice_with_long_streams(env, fam, tr):
     A = o["abs"].mean() / n
     assert abs(res[0] - qbar) <= TOL * A
     assert abs(res[1] - sig) <= max(1e-9 * sig, 2e-12 * A)
+
+
+@pytest.mark.parametrize("form", ["regular", "like"])
+def test_complex_family_full_size_tiles_match_oracle(env, form):
+    """The complex deformed family (the d = 5 Feynman-parameter workload of the
+    benchmark's feynman object, and the configuration's literal polynomials) on
+    n = 10,560,653 with m = 32: three tiles of the full launch, real and imaginary
+    partials, against the oracle at 1e-12 of the tile's sum |g|."""
+    q, torch, dev, tab = env
+    n = bench.N_LATTICE
+    fam, d, tr, fl, _ = bench.workload_items(0, workload="feynman" if form == "regular"
+                                             else "feynman_like")[1]
+    D = O.shifts(SEED + 1, M, d)
+    z = tab.z_for(n)[:d]
+    Dd = torch.from_numpy(D.astype(np.int64)).to(dev)
+    r = q.rule(n, z, Dd, tr)
+    fd = q.Integrand.polynomial(fl).device_struct(dev)
+    ws = torch.empty(q.sums_workspace_bytes(r, True, 0, n), dtype=torch.uint8, device=dev)
+    sums = torch.zeros(4 * M, dtype=torch.float64, device=dev)
+    q.sums(fd, r, 0, n, ws, sums)
+    torch.cuda.synchronize()
+    tiles, ppt = q.sums_tile_count(n, M)
+    part = ws[: 2 * tiles * M * 16].view(torch.float64).cpu().numpy().reshape(2, tiles, M, 2)
+    worst = 0.0
+    for t in _picks(tiles, 3, 7 + len(form)):
+        a, b = t * ppt, min(t * ppt + ppt, n)
+        o = O.shift_sums(O.feynman_complex(fl), tr, n, z, D, i0=a, i1=b)
+        for comp, key in ((0, "re"), (1, "im")):
+            S_gpu = part[comp, t, :, 0] + part[comp, t, :, 1]
+            S_or = o[key][:, 0] + o[key][:, 1]
+            fin = np.isfinite(S_or)
+            worst = max(worst, _check_sums(S_gpu[fin], S_or[fin], o["abs"][fin], (form, t, key)))
+            assert np.array_equal(np.isfinite(S_gpu), fin)
+    print(f"[parity] complex {form} tiles n={n}: max |dS|/A = {worst:.2e}")
+
+
+def test_batch_at_config4_sizes_equals_single_launches(env):
+    """Sector integrals with n log-uniform in [1e4, 1e8] (the batching configuration's
+    range) in one batched launch with the default shape: every item's sums equal a
+    qmc_sums call on that item bit for bit, and one tile of the largest item matches the
+    oracle."""
+    q, torch, dev, tab = env
+    rng = np.random.default_rng(11)
+    entries, keep = [], []
+    for i in range(5):
+        d = int(rng.integers(3, 9))
+        fl = W.sector_like(500 + i, d, int(rng.integers(10, 401)), int(rng.integers(10, 401)))
+        n = q.get_next_n(tab, int(np.exp(rng.uniform(np.log(1e4), np.log(1e8)))))
+        if i == 0:
+            n = 104019611
+        D = q.make_shifts(600 + i, M, d)
+        Dd = torch.from_numpy(D.astype(np.int64)).to(dev)
+        r = q.rule(n, tab.z_for(n)[:d], Dd, ("korobov", 3))
+        f = q.Integrand.polynomial(fl)
+        entries.append((f.device_struct(dev), r, 0, n))
+        keep.append((fl, D, Dd, f))
+    b = q.Batch(entries)
+    ws = torch.empty(b.workspace_bytes(), dtype=torch.uint8, device=dev)
+    bsums = torch.zeros(len(entries), 4 * M, dtype=torch.float64, device=dev)
+    b.sums(ws, bsums)
+    torch.cuda.synchronize()
+    got = bsums.cpu().numpy()
+    for i, (fd, r, _, n) in enumerate(entries):
+        wsi = torch.empty(q.sums_workspace_bytes(r, False, 0, n), dtype=torch.uint8, device=dev)
+        one = torch.zeros(4 * M, dtype=torch.float64, device=dev)
+        q.sums(fd, r, 0, n, wsi, one)
+        torch.cuda.synchronize()
+        assert np.array_equal(got[i, : 2 * M], one.cpu().numpy()[: 2 * M]), i
+        if i == 0:
+            tiles, ppt = q.sums_tile_count(n, M)
+            part = wsi[: tiles * M * 16].view(torch.float64).cpu().numpy().reshape(tiles, M, 2)
+            t = tiles // 2
+            fl, D = keep[0][0], keep[0][1]
+            o = O.shift_sums(O.from_feynman(fl), ("korobov", 3), n, tab.z_for(n)[:fl.d], D,
+                             i0=t * ppt, i1=min(t * ppt + ppt, n))
+            worst = _check_sums(part[t, :, 0] + part[t, :, 1], o["re"][:, 0] + o["re"][:, 1],
+                                o["abs"], ("sector", t))
+            print(f"[parity] sector tile n={n}: max |dS|/A = {worst:.2e}")

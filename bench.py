@@ -426,8 +426,13 @@ def run_gpu(args, rank: int, world: int):
             q.finalize(sums[i], M_SHIFTS, n, cplx, res[i], None, s)
         if time_kernels:
             torch.cuda.synchronize(dev)
-            kt = sum(a.elapsed_time(b) for a, b in ev_k)
+            per = [a.elapsed_time(b) for a, b in ev_k]
+            for i, v in enumerate(per):
+                item_ms[i] += v
+            kt = sum(per)
         return kt
+
+    item_ms = [0.0] * len(prepared)
 
     for _ in range(args.warmup):
         step(False)
@@ -505,6 +510,9 @@ def run_gpu(args, rank: int, world: int):
         "total_ms": total_ms, "step_ms": step_ms, "evals_per_step": evals_per_step,
         "flops_per_step": flops_per_step, "muls_per_step": muls_per_step,
         "tensor_flops_per_step": tensor_flops_per_step,
+        "kernel_ms_per_item": ({f"{fam}:{d}:{tr[0]}{tr[1] if len(tr) > 1 else ''}": ms / args.steps
+                                for (fam, d, tr, _, _), ms in zip(items, item_ms)}
+                               if args.kernel_events and graph is None else None),
         "kernel_ms_per_launch": k_per_launch_ms, "unit_peaks": peaks,
         "clocks": clocks, "e2e_total_ms": e2e_total, "e2e_steps": args.e2e_steps,
         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(items) * ((8 if cplx else 4) * 8 + 2 * 8),
@@ -1020,6 +1028,8 @@ def main():
                     help="server step budget in evaluations (0: all running requests each step)")
     ap.add_argument("--batch-count", type=int, default=2000)
     ap.add_argument("--batch-nmax", type=float, default=1e8)
+    ap.add_argument("--per-item", action="store_true",
+                    help="add each integral's mean lattice-sum launch time (ms) to the line")
     ap.add_argument("--graph", action="store_true",
                     help="replay each timed step from a CUDA graph (host launch work out of "
                          "the timed region; no per-launch kernel events)")
@@ -1102,6 +1112,7 @@ def main():
             "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
                        "reasons": clk.get("reasons")},
             "nonfinite": r["nonfinite"],
+            **({"kernel_ms_per_item": r["kernel_ms_per_item"]} if args.per_item else {}),
         })
         if world == 1 and args.cpu_budget > 0:
             line["cpu_baseline"] = cpu_baseline(args.cpu_budget, workload_items(0, args.only, args.workload))

@@ -178,25 +178,62 @@ def feynman_flops_per_eval(fl) -> int:
     return derivs + complex_vals + deform + lu + 2 * 9 + 12 + 4
 
 
+FEYN_FIXED_DIMS = range(3, 7)      # dimensions whose contractions run in fixed point
+
+
+def feynman_fixed_int_mul_per_eval(d: int) -> int:
+    """32-bit multiplies of the fixed-point part of one complex evaluation (d = 3..6): the
+    Hessian 2 F2 + 6 F3 x (d per entry of the upper triangle) and the contractions H x, F2 x,
+    U2 x (d^2 each), one truncated 64-bit high product (MUL_HI) apiece."""
+    if d not in FEYN_FIXED_DIMS:
+        return 0
+    return MUL_HI * (d * d * (d + 1) // 2 + 3 * d * d)
+
+
+def feynman_int_mul_per_eval(transform, d: int) -> int:
+    """32-bit multiplies of one complex evaluation: the integer Korobov<r,r> map and weight
+    (as int_mul_per_eval counts them) and the fixed-point contractions."""
+    kind = transform[0]
+    r = transform[1] if kind == "korobov" else 0
+    per = feynman_fixed_int_mul_per_eval(d)
+    if kind == "korobov" and 1 <= r <= 6 and (len(transform) < 3 or transform[2] == r):
+        per += korobov_map_muls(r) * d + korobov_weight_muls(r)
+    return per
+
+
 def feynman_tensor_flops_per_eval(d: int) -> int:
     """FP64 work of one evaluation of the complex deformed integrand in the symmetric-tensor
     form the kernel evaluates for deg U <= 2, deg F <= 3 (qmc_poly.cuh), with fma = 2 and
     add/mul/div/sqrt = 1, for a = 1 and a half-integer b (b = 2.5): the Hessian 2 F2 + 6 F3 x,
-    gradient, F(x), U(x) and grad U, the deformation y = -lam x (1 - x) g, F(z) and U(z) by the
-    exact Taylor series, det J by elimination without pivoting (the first column on purely
-    imaginary entries), 1 / (F^2 sqrt F) by the principal root, the products with U and
-    det J, the weight and the accumulation.  It does not grow with the number of monomials."""
+    gradient and grad U (in fixed point for d = 3..6, so no FP64 work there; FP64 otherwise),
+    F(x) and U(x) (the nested form in FP64 for d = 3..6), the deformation
+    y = -lam x (1 - x) g, F(z) and U(z) by the exact Taylor series (for d = 3..6 y.H y over
+    the upper triangle and the cubic and quadratic parts at y by nested forms), det J by elimination
+    without pivoting (the first column on purely imaginary entries), 1 / (F^2 sqrt F) by the
+    principal root, the products with U and det J, the weight and the accumulation.  It does
+    not grow with the number of monomials."""
     P = d * (d + 1) // 2
     fma, mul, add, special = 0, 0, 0, 0
-    fma += P * (d + 1)                                   # Hessian entries
-    fma += d * (3 * d + 6)                               # gradient, F(x), U(x), grad U
-    add += 2 * d + 2
+    if d in FEYN_FIXED_DIMS:
+        fma += d * (d + 1) * (d + 2) // 6 + P + d        # F(x), nested form
+        fma += P + d                                     # U(x), nested form
+    else:
+        fma += P * (d + 1)                               # Hessian entries
+        fma += d * (3 * d + 6)                           # gradient, F(x), U(x), grad U
+        add += 2 * d + 2
     add += d                                             # 1 - x
     mul += 3 * d                                         # -lam x (1 - x), y = xo g
-    fma += d * (2 * d + 4) + P * (d + 1)                 # y.H y, y.U2 y, g.y, gradU.y, F3[y,y,y]
-    mul += 2 * P
-    fma += 2
-    add += 1                                             # F(z), U(z)
+    if d in FEYN_FIXED_DIMS:
+        fma += (P - d) + 2 * d + 2 * d                   # y.H y (upper triangle), g.y, gradU.y
+        mul += d
+        fma += d * (d + 1) * (d + 2) // 6 + 2 * P + 2 * d   # F3[y,y,y], y.U2 y nested
+        fma += 1
+        add += 2                                         # F(z), U(z)
+    else:
+        fma += d * (2 * d + 4) + P * (d + 1)             # y.H y, y.U2 y, g.y, gradU.y, F3[y,y,y]
+        mul += 2 * P
+        fma += 2
+        add += 1                                         # F(z), U(z)
     mul += d * d + d                                     # Jacobian entries
     fma += 2 * d
     fma += 1 + (d - 1) * 2 * (d - 1)                     # first column
@@ -407,8 +444,8 @@ def run_gpu(args, rank: int, world: int):
     evals_per_step = len(items) * n * M_SHIFTS
     flops_per_step = sum(feynman_flops_per_eval(c) if fam == FEYNMAN_FAMILY else
                          fp64_flops_per_eval(fam, tr, d) for fam, d, tr, c, _ in items) * n * M_SHIFTS
-    muls_per_step = sum(0 if fam == FEYNMAN_FAMILY else int_mul_per_eval(fam, tr, d, c)
-                        for fam, d, tr, c, _ in items) * n * M_SHIFTS
+    muls_per_step = sum(feynman_int_mul_per_eval(tr, d) if fam == FEYNMAN_FAMILY else
+                        int_mul_per_eval(fam, tr, d, c) for fam, d, tr, c, _ in items) * n * M_SHIFTS
     tensor_flops_per_step = sum(feynman_tensor_flops_per_eval(d) if fam == FEYNMAN_FAMILY else 0
                                 for fam, d, tr, c, _ in items) * n * M_SHIFTS
 
@@ -903,11 +940,16 @@ def roofline(r, workload: str):
         kf = r["tensor_flops_per_step"] / launches / sec / 1e9
         fp64["note"] = ("term-by-term FP64 work of U, F and their derivatives "
                         "(feynman_flops_per_eval) against the measured FP64 FMA rate")
+        muls = r["muls_per_step"] / launches / sec / 1e9
+        int_pipe = {"achieved": round(muls, 1), "peak": round(pk["int_mul_gops"], 1),
+                    "unit": "G int32 mul/s", "frac": round(muls / pk["int_mul_gops"], 4),
+                    "work": "feynman_int_mul_per_eval: integer Korobov map and weight, "
+                            "fixed-point Hessian and contractions"}
         return {"bound": "alu", "unit": "GFLOP/s", "achieved": round(kf, 1),
                 "peak": round(pk["fp64_gflops"], 1), "frac": round(kf / pk["fp64_gflops"], 4),
                 "peak_source": "measured FP64 FMA rate (qmc_probe_units), 2 flops per FMA",
-                "work": "feynman_tensor_flops_per_eval: the symmetric-tensor form",
-                "fp64_equivalent": fp64, **common}
+                "work": "feynman_tensor_flops_per_eval: the symmetric-tensor form's FP64 part",
+                "int_pipe": int_pipe, "fp64_equivalent": fp64, **common}
     muls = r["muls_per_step"] / launches / sec / 1e9            # G 32-bit multiplies/s
     return {"bound": "alu", "unit": "G int32 mul/s", "achieved": round(muls, 1),
             "peak": round(pk["int_mul_gops"], 1), "frac": round(muls / pk["int_mul_gops"], 4),

@@ -19,6 +19,7 @@
 #pragma once
 #include <cstdint>
 
+#include "qmc_fixed.cuh"
 #include "qmc_fp.cuh"
 #include "qmc_params.cuh"
 
@@ -46,6 +47,10 @@ struct PolyShared {
     uint16_t ukey2[kMaxTerms], fkey2[kMaxTerms];   // dense keys as a quadratic (0xFFFF: degree 3)
     int maxdeg_u, maxdeg_f;
     int feyn_dense;   // complex family: symmetric-tensor form (see stage_feynman_tensors)
+    // complex family, d <= kFeynFixedMaxDim: the tensors also in signed fixed point, F's
+    // as round(c 2^sf) at u[3 kMaxTerms + e], U's as round(c 2^su) at u[kMaxTerms + e];
+    // the nested-form coefficients of F and U after their FP64 tensors (feyn_add_horner)
+    int feyn_fixed, sf, su;
 };
 
 // Symmetric-tensor form of the complex family (deg U <= 2, deg F <= 3, d <= kFeynDenseMaxDim):
@@ -55,6 +60,10 @@ struct PolyShared {
 // permutations of its factors).  Layout in buf: U at [0]: u0, u1[d], U2[d][d];
 // F at [2 kMaxTerms]: f0, f1[d], F2[d][d], 6 F3[pair(i <= j)][k] (row-major upper triangle).
 constexpr int kFeynDenseMaxDim = 11;   // 1 + d + d^2 + d^2 (d+1)/2 <= 2 kMaxTerms
+// The fixed-point copies sit in the halves of the U and F blocks the tensors leave free
+// (1 + d + d^2 + d^2 (d+1)/2 <= kMaxTerms for d <= 6), the nested-form coefficients of
+// the values after the FP64 tensors (1 + d + d^2 + d^2 (d+1)/2 + C(d+3, 3) <= kMaxTerms).
+constexpr int kFeynFixedMaxDim = 6;
 __device__ __forceinline__ int feyn_pair(int i, int j, int d) {   // i <= j
     return i * d - i * (i - 1) / 2 + (j - i);
 }
@@ -148,6 +157,26 @@ __device__ __forceinline__ void feyn_add_term(double *base, double *t3, const in
     }
 }
 
+// Adds coefficient c of monomial e (degree <= 3) to the coefficient list of the nested
+// (Horner) form P = c0 + sum_i x_i (c1_i + sum_{j >= i} x_j (c2_ij + sum_{k >= j} c3_ijk x_k)),
+// laid out as c0, c1[d], c2 over i <= j, c3 over i <= j <= k (lexicographic).
+__device__ __forceinline__ void feyn_add_horner(double *h, const int32_t *e, int d, double c) {
+    int f[3];
+    int n = 0;
+    for (int k = 0; k < d; ++k)
+        for (int q = 0; q < e[k] && n < 3; ++q) f[n++] = k;
+    int slot = 0;
+    if (n >= 1) slot = 1 + f[0];
+    if (n >= 2) slot = 1 + d + feyn_pair(f[0], f[1], d);
+    if (n == 3) {
+        int off = 0;   // triples with first index below f[0], then pairs (j, k) from f[0]
+        for (int i = 0; i < f[0]; ++i) off += (d - i) * (d - i + 1) / 2;
+        for (int j = f[0]; j < f[1]; ++j) off += d - j;
+        slot = 1 + d + d * (d + 1) / 2 + off + (f[2] - f[1]);
+    }
+    h[slot] += c;
+}
+
 // FP64 operations per evaluation of the two forms of the complex family (derivatives,
 // values at the complex point; the Jacobian and powers are common).
 __device__ __forceinline__ bool feyn_tensor_cheaper(const PolyShared &ps, const int32_t *uexp,
@@ -183,6 +212,7 @@ __device__ __forceinline__ void stage_poly(const P &p, PolyShared &ps, bool allo
         ps.lam = p.lam;
         ps.maxdeg_u = 0;
         ps.maxdeg_f = 0;
+        ps.feyn_fixed = 0;
     }
     __syncthreads();
     // keys as a cubic in d+1 variables (degree of each monomial recorded)
@@ -232,6 +262,37 @@ __device__ __forceinline__ void stage_poly(const P &p, PolyShared &ps, bool allo
             double *fb = ps.buf.v + 2 * kMaxTerms;
             for (int q = 0; q < p.nf; ++q)
                 feyn_add_term(fb, fb + nU, p.fexp + (size_t)q * d, d, p.fcoef[q]);
+            // Scales of the fixed-point form: with B the sum of |entries| of a polynomial's
+            // tensors, every quantity feyn_fixed_parts forms at x in [0, 1]^d (Hessian
+            // entries, contractions, gradient, value, and their partial sums) is below
+            // (2d + 1) B <= 16 B, so c 2^s with 16 B 2^s < 2^62 cannot overflow.
+            double bf = 0.0, bu = 0.0;
+            for (int e = 0; e < nF; ++e) bf += fabs(fb[e]);
+            for (int e = 0; e < nU; ++e) bu += fabs(ps.buf.v[e]);
+            int ok = d <= kFeynFixedMaxDim && bf > 0.0 && bf < 1e300 && bu > 0.0 && bu < 1e300;
+            const int sf = ok ? 61 - ilogb(16.0 * bf) : 0;
+            const int su = ok ? 61 - ilogb(16.0 * bu) : 0;
+            ok = ok && sf >= 32 && su >= 32 && sf <= 120 && su <= 120;
+            ps.feyn_fixed = ok;
+            ps.sf = sf;
+            ps.su = su;
+        }
+        __syncthreads();
+        if (ps.feyn_fixed) {
+            for (int e = tid; e < nF; e += blockDim.x)
+                ps.buf.u[3 * kMaxTerms + e] = (uint64_t)llrint(ldexp(ps.buf.v[2 * kMaxTerms + e], ps.sf));
+            for (int e = tid; e < nU; e += blockDim.x)
+                ps.buf.u[kMaxTerms + e] = (uint64_t)llrint(ldexp(ps.buf.v[e], ps.su));
+            // the values F(x), U(x) in FP64 through the nested form (see feyn_fixed_parts)
+            double *hu = ps.buf.v + nU, *hf = ps.buf.v + 2 * kMaxTerms + nF;
+            const int nHu = 1 + d + d * (d + 1) / 2, nHf = nHu + d * (d + 1) * (d + 2) / 6;
+            for (int e = tid; e < nHu; e += blockDim.x) hu[e] = 0.0;
+            for (int e = tid; e < nHf; e += blockDim.x) hf[e] = 0.0;
+            __syncthreads();
+            if (tid == 0) {
+                for (int q = 0; q < p.nu; ++q) feyn_add_horner(hu, p.uexp + (size_t)q * d, d, p.ucoef[q]);
+                for (int q = 0; q < p.nf; ++q) feyn_add_horner(hf, p.fexp + (size_t)q * d, d, p.fcoef[q]);
+            }
         }
         return;
     }
@@ -478,6 +539,120 @@ __device__ __forceinline__ void feynman_combine(cplx U, cplx F, cplx det, double
     im = v.im;
 }
 
+// Signed fixed point for the tensor contractions of the symmetric-tensor form: a value v
+// is held as the int64 round(v 2^s) with one scale s per polynomial, a coordinate x in
+// [0, 1] as the uint64 X = x 2^64.  Products go through the integer multiply pipe.
+//   c X / 2^64 for signed c: the unsigned high word of (c mod 2^64) X, minus X when c < 0.
+__device__ __forceinline__ int64_t smulhi_x(int64_t c, uint64_t X) {
+    const uint64_t h = mulhi_trunc((uint64_t)c, X);
+    return (int64_t)(c < 0 ? h - X : h);
+}
+// x in [0, 1] to x 2^64, truncated (x = 1 saturates to 2^64 - 1).  For 0 < x < 1 with
+// biased exponent E <= 1022, x 2^64 is the 64-bit mantissa shifted right by 1022 - E.
+// The range tests compare the bit pattern as a signed integer (non-negative doubles order
+// like their bits; negative ones have the sign bit set), which keeps them off the FP64 pipe.
+__device__ __forceinline__ uint64_t unit_to_fixed64(double x) {
+    const long long b = __double_as_longlong(x);
+    if (b >= 0x3FF0000000000000ll) return ~0ull;   // x >= 1
+    if (b <= 0) return 0ull;                       // x <= 0
+    const int r = 1022 - (int)(b >> 52);
+    const uint64_t m = ((uint64_t)b << 11) | 0x8000000000000000ull;
+    return r >= 64 ? 0ull : (m >> r);
+}
+// v 2^-s to double, truncated toward zero, by integer operations.
+__device__ __forceinline__ double fixed_s64_to_double(int64_t v, int s) {
+    const uint64_t sign = (uint64_t)v & 0x8000000000000000ull;
+    const uint64_t a = v < 0 ? (uint64_t)0 - (uint64_t)v : (uint64_t)v;
+    if (!a) return 0.0;
+    const int lz = __clzll(a);
+    const uint64_t m = a << lz;   // a 2^lz in [2^63, 2^64): v = m 2^(63 - lz - s) / 2^63
+    const uint64_t be1 = (uint64_t)(1085 - lz - s);   // biased exponent minus one
+    return __longlong_as_double((long long)(sign | ((be1 << 52) + (m >> 11))));
+}
+
+// Hessian and gradient of F and grad U of the symmetric-tensor form at x, as
+// feynman_value_dense forms them in FP64, here in the fixed point above (same formulas:
+// H_ij = 2 F2_ij + sum_k (6 F3)_ijk x_k, g_i = f1_i + (F2 x)_i + (H x)_i / 2,
+// grad U_i = u1_i + 2 (U2 x)_i).  A product is off by under 4.5 units of 2^-s
+// (mulhi_trunc's bound, the dropped fraction, the rounded entry and the truncated X), so
+// for d <= 6 each result is within 2^8 units, i.e. 2^-49 of the sum B of the polynomial's
+// |entries| (2^-s <= 2^-57 B by the choice of s); every partial sum stays below
+// 3 B < 2^62 2^-s.  These enter the integrand only through the deformation
+// y = -lam x (1 - x) g and the Jacobian, where an error small against B is small against
+// the terms it joins.  The values F(x) and U(x) need relative accuracy instead: near the
+// zero set of F, F(x) is many orders below B, and its error there is raised to the power
+// -b.  They stay in FP64, by the nested form of the monomial list
+// (c0 + sum_i x_i (c1_i + sum_{j >= i} x_j (c2_ij + sum_{k >= j} c3_ijk x_k))).
+template <int D>
+__device__ __forceinline__ void feyn_fixed_parts(const double *x, const PolyShared &ps,
+                                                 double *H, double *g, double *gU,
+                                                 double &Fx, double &Ux) {
+    constexpr int nU = 1 + D + D * D, nF = nU + D * D * (D + 1) / 2;
+    const int64_t *ff = reinterpret_cast<const int64_t *>(ps.buf.u + 3 * kMaxTerms);
+    const int64_t *uf = reinterpret_cast<const int64_t *>(ps.buf.u + kMaxTerms);
+    const int64_t *f1 = ff + 1, *F2 = ff + 1 + D, *F3 = ff + 1 + D + D * D;
+    const int64_t *u1 = uf + 1, *U2 = uf + 1 + D;
+    const int sf = ps.sf, su = ps.su;
+    uint64_t X[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) X[k] = unit_to_fixed64(x[k]);
+    int64_t Hq[D * D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = i; j < D; ++j) {
+            const int64_t *t = F3 + feyn_pair(i, j, D) * D;
+            int64_t s = 2 * F2[i * D + j];
+#pragma unroll
+            for (int k = 0; k < D; ++k) s += smulhi_x(t[k], X[k]);
+            Hq[i * D + j] = s;
+            Hq[j * D + i] = s;
+        }
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        int64_t hx = 0, qx = 0, px = 0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            hx += smulhi_x(Hq[i * D + j], X[j]);
+            qx += smulhi_x(F2[i * D + j], X[j]);
+            px += smulhi_x(U2[i * D + j], X[j]);
+        }
+        g[i] = fixed_s64_to_double(f1[i] + qx + (hx >> 1), sf);
+        gU[i] = fixed_s64_to_double(u1[i] + 2 * px, su);
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = i; j < D; ++j) {
+            const double h = fixed_s64_to_double(Hq[i * D + j], sf);
+            H[i * D + j] = h;
+            H[j * D + i] = h;
+        }
+    // values: nested form, coefficients after the FP64 tensors
+    const double *hu = ps.buf.v + nU, *hf = ps.buf.v + 2 * kMaxTerms + nF;
+    const double *c2u = hu + 1 + D;
+    const double *c2f = hf + 1 + D, *c3f = hf + 1 + D + D * (D + 1) / 2;
+    double Fv = hf[0], Uv = hu[0];
+    int p2 = 0, p3 = 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        double tf = hf[1 + i], tu = hu[1 + i];
+#pragma unroll
+        for (int j = i; j < D; ++j) {
+            double tij = c2f[p2];
+#pragma unroll
+            for (int k = j; k < D; ++k) tij = fma(c3f[p3++], x[k], tij);
+            tf = fma(tij, x[j], tf);
+            tu = fma(c2u[p2], x[j], tu);
+            ++p2;
+        }
+        Fv = fma(tf, x[i], Fv);
+        Uv = fma(tu, x[i], Uv);
+    }
+    Fx = Fv;
+    Ux = Uv;
+}
+
 // Symmetric-tensor form (deg U <= 2, deg F <= 3).  At the real point x:
 //   H_ij = 2 F2_ij + 6 sum_k F3_ijk x_k,  g_i = f1_i + (F2 x)_i + (H x)_i / 2,
 //   F(x) = f0 + sum_i x_i (f1_i + (H x)_i / 6 + 2 (F2 x)_i / 3),
@@ -486,7 +661,7 @@ __device__ __forceinline__ void feynman_combine(cplx U, cplx F, cplx det, double
 //   U(z) = U(x) - y.U2 y + i grad U.y,  grad U = u1 + 2 U2 x.
 // DT > 0: the dimension as a compile-time constant (unrolled loops, per-thread arrays of
 // d entries that can stay in registers); DT = 0: d at run time.  Same operations, same order.
-template <int DT>
+template <int DT, bool FX = false>
 static __device__ __noinline__ void feynman_value_dense(const double *xin, int d_rt,
                                                         const PolyShared &ps, double &re,
                                                         double &im,
@@ -501,38 +676,43 @@ static __device__ __noinline__ void feynman_value_dense(const double *xin, int d
     double H[DA * DA];
 #pragma unroll
     for (int k = 0; k < d; ++k) x[k] = xin[k];
-    // Hessian of F (symmetric)
-#pragma unroll
-    for (int i = 0; i < d; ++i)
-#pragma unroll
-        for (int j = i; j < d; ++j) {
-            const double *t = F3 + feyn_pair(i, j, d) * d;
-            double s = 0.0;
-#pragma unroll
-            for (int k = 0; k < d; ++k) s = fma(t[k], x[k], s);
-            const double h = fma(2.0, F2[i * d + j], s);   // s = (6 F3 x)_ij
-            H[i * d + j] = h;
-            H[j * d + i] = h;
-        }
-    // gradient, F(x), U(x), grad U
     double Fx = 0.0, Ux = 0.0;
     double gU[DA];
+    if constexpr (FX) {
+        static_assert(DT > 0 && DT <= kFeynFixedMaxDim, "fixed point needs a compiled dimension");
+        feyn_fixed_parts<DT>(x, ps, H, g, gU, Fx, Ux);
+    } else {
+        // Hessian of F (symmetric)
 #pragma unroll
-    for (int i = 0; i < d; ++i) {
-        double hx = 0.0, qx = 0.0, px = 0.0;
+        for (int i = 0; i < d; ++i)
 #pragma unroll
-        for (int j = 0; j < d; ++j) {
-            hx = fma(H[i * d + j], x[j], hx);
-            qx = fma(F2[i * d + j], x[j], qx);
-            px = fma(U2[i * d + j], x[j], px);
+            for (int j = i; j < d; ++j) {
+                const double *t = F3 + feyn_pair(i, j, d) * d;
+                double s = 0.0;
+#pragma unroll
+                for (int k = 0; k < d; ++k) s = fma(t[k], x[k], s);
+                const double h = fma(2.0, F2[i * d + j], s);   // s = (6 F3 x)_ij
+                H[i * d + j] = h;
+                H[j * d + i] = h;
+            }
+        // gradient, F(x), U(x), grad U
+#pragma unroll
+        for (int i = 0; i < d; ++i) {
+            double hx = 0.0, qx = 0.0, px = 0.0;
+#pragma unroll
+            for (int j = 0; j < d; ++j) {
+                hx = fma(H[i * d + j], x[j], hx);
+                qx = fma(F2[i * d + j], x[j], qx);
+                px = fma(U2[i * d + j], x[j], px);
+            }
+            g[i] = fma(0.5, hx, f1[i] + qx);
+            Fx = fma(x[i], fma(hx, 1.0 / 6.0, fma(qx, 2.0 / 3.0, f1[i])), Fx);
+            gU[i] = fma(2.0, px, u1[i]);
+            Ux = fma(x[i], u1[i] + px, Ux);
         }
-        g[i] = fma(0.5, hx, f1[i] + qx);
-        Fx = fma(x[i], fma(hx, 1.0 / 6.0, fma(qx, 2.0 / 3.0, f1[i])), Fx);
-        gU[i] = fma(2.0, px, u1[i]);
-        Ux = fma(x[i], u1[i] + px, Ux);
+        Fx += fb[0];
+        Ux += ub[0];
     }
-    Fx += fb[0];
-    Ux += ub[0];
     // deformation: xo holds -lam x (1 - x)
     const double lam = ps.lam;
 #pragma unroll
@@ -541,30 +721,63 @@ static __device__ __noinline__ void feynman_value_dense(const double *xin, int d
         y[k] = xo[k] * g[k];
     }
     // F(z), U(z)
-    double yHy = 0.0, gy = 0.0, yU2y = 0.0, gUy = 0.0, t3 = 0.0;
+    cplx Fz, Uz;
+    if constexpr (FX) {
+        // y.H y over the upper triangle; the quadratic part of U and the cubic part of F
+        // at y by their nested forms (the same monomial coefficients as F(x), U(x))
+        constexpr int nU = 1 + DA + DA * DA, nF = nU + DA * DA * (DA + 1) / 2;
+        const double *c2u = ps.buf.v + nU + 1 + DA;
+        const double *c3f = ps.buf.v + 2 * kMaxTerms + nF + 1 + DA + DA * (DA + 1) / 2;
+        double yHy = 0.0, gy = 0.0, gUy = 0.0, qU = 0.0, cF = 0.0;
+        int p2 = 0, p3 = 0;
 #pragma unroll
-    for (int i = 0; i < d; ++i) {
-        double hy = 0.0, uy = 0.0;
+        for (int i = 0; i < DA; ++i) {
+            double t = 0.0;
 #pragma unroll
-        for (int j = 0; j < d; ++j) {
-            hy = fma(H[i * d + j], y[j], hy);
-            uy = fma(U2[i * d + j], y[j], uy);
+            for (int j = i + 1; j < DA; ++j) t = fma(H[i * DA + j], y[j], t);
+            yHy = fma(y[i], fma(2.0, t, H[i * DA + i] * y[i]), yHy);
+            gy = fma(g[i], y[i], gy);
+            gUy = fma(gU[i], y[i], gUy);
+            double tf = 0.0, tu = 0.0;
+#pragma unroll
+            for (int j = i; j < DA; ++j) {
+                double tij = 0.0;
+#pragma unroll
+                for (int k = j; k < DA; ++k) tij = fma(c3f[p3++], y[k], tij);
+                tf = fma(tij, y[j], tf);
+                tu = fma(c2u[p2++], y[j], tu);
+            }
+            cF = fma(tf, y[i], cF);
+            qU = fma(tu, y[i], qU);
         }
-        yHy = fma(y[i], hy, yHy);
-        yU2y = fma(y[i], uy, yU2y);
-        gy = fma(g[i], y[i], gy);
-        gUy = fma(gU[i], y[i], gUy);
+        Fz = {fma(-0.5, yHy, Fx), gy - cF};
+        Uz = {Ux - qU, gUy};
+    } else {
+        double yHy = 0.0, gy = 0.0, yU2y = 0.0, gUy = 0.0, t3 = 0.0;
 #pragma unroll
-        for (int j = i; j < d; ++j) {
-            const double *t = F3 + feyn_pair(i, j, d) * d;
-            double s = 0.0;
+        for (int i = 0; i < d; ++i) {
+            double hy = 0.0, uy = 0.0;
 #pragma unroll
-            for (int k = 0; k < d; ++k) s = fma(t[k], y[k], s);
-            t3 = fma((i == j ? 1.0 : 2.0) * y[i] * y[j], s, t3);
+            for (int j = 0; j < d; ++j) {
+                hy = fma(H[i * d + j], y[j], hy);
+                uy = fma(U2[i * d + j], y[j], uy);
+            }
+            yHy = fma(y[i], hy, yHy);
+            yU2y = fma(y[i], uy, yU2y);
+            gy = fma(g[i], y[i], gy);
+            gUy = fma(gU[i], y[i], gUy);
+#pragma unroll
+            for (int j = i; j < d; ++j) {
+                const double *t = F3 + feyn_pair(i, j, d) * d;
+                double s = 0.0;
+#pragma unroll
+                for (int k = 0; k < d; ++k) s = fma(t[k], y[k], s);
+                t3 = fma((i == j ? 1.0 : 2.0) * y[i] * y[j], s, t3);
+            }
         }
+        Fz = {fma(-0.5, yHy, Fx), fma(t3, -1.0 / 6.0, gy)};   // t3 = 6 F3[y, y, y]
+        Uz = {Ux - yU2y, gUy};
     }
-    const cplx Fz = {fma(-0.5, yHy, Fx), fma(t3, -1.0 / 6.0, gy)};   // t3 = 6 F3[y, y, y]
-    const cplx Uz = {Ux - yU2y, gUy};
     if (Fz.im > 0.0) ++signfail;
     const cplx det = feynman_jacobian_det<DT>(x, xo, g, H, d, lam);
     feynman_combine(Uz, Fz, det, ps.pa, ps.pb, re, im);
@@ -575,6 +788,15 @@ static __device__ __noinline__ void feynman_value(const double *xin, int d, cons
                                            unsigned long long &signfail) {
     if (ps.feyn_dense) {
         // the symmetric-tensor form with the dimension compiled in for the common sizes
+        if (ps.feyn_fixed) {
+            switch (d) {
+            case 3: feynman_value_dense<3, true>(xin, d, ps, re, im, signfail); return;
+            case 4: feynman_value_dense<4, true>(xin, d, ps, re, im, signfail); return;
+            case 5: feynman_value_dense<5, true>(xin, d, ps, re, im, signfail); return;
+            case 6: feynman_value_dense<6, true>(xin, d, ps, re, im, signfail); return;
+            default: break;
+            }
+        }
         switch (d) {
         case 3: feynman_value_dense<3>(xin, d, ps, re, im, signfail); return;
         case 4: feynman_value_dense<4>(xin, d, ps, re, im, signfail); return;

@@ -91,3 +91,23 @@ def test_int_multiply_work_is_positive_for_the_benchmark():
     for fam, d, tr, c, _ in bench.workload_items():
         assert bench.int_mul_per_eval(fam, tr, d, c) > 0
 
+
+
+def test_complex_family_work_split():
+    """d = 3..6 evaluate the Hessian and the contractions in fixed point: 150 truncated
+    high products for d = 5 (75 Hessian terms, 25 each for H x, F2 x, U2 x) on top of the
+    Korobov-3 map and weight; the FP64 count keeps the nested-form values F(x) (55 fused
+    multiply-adds) and U(x) (20) of that part, and the Taylor terms at y take the upper
+    triangle and the nested forms.  d = 7 keeps the all-FP64 form."""
+    assert bench.feynman_fixed_int_mul_per_eval(5) == bench.MUL_HI * 150
+    assert bench.feynman_int_mul_per_eval(("korobov", 3), 5) == (
+        bench.MUL_HI * 150 + 5 * bench.korobov_map_muls(3) + bench.korobov_weight_muls(3))
+    assert bench.feynman_fixed_int_mul_per_eval(7) == 0
+    # FP64 form for d = 5: Hessian 15 * 6 and gradient/values 5 * 21 fma, 12 adds; Taylor
+    # terms 5 * 14 + 15 * 6 + 2 fma, 30 mul, 1 add
+    fp64_form = 2 * (15 * 6 + 5 * 21) + 12 + 2 * (70 + 90 + 2) + 30 + 1
+    # values 55 + 20 fma; Taylor terms 10 + 10 + 10 fma and 5 mul (y.H y, g.y, grad U.y),
+    # 35 + 30 + 10 fma (nested cubic and quadratic at y), 1 fma, 2 adds
+    fixed_form = 2 * (55 + 20) + 2 * (30 + 75 + 1) + 5 + 2
+    assert bench.feynman_tensor_flops_per_eval(5) == 1139 - fp64_form + fixed_form
+    assert bench.feynman_tensor_flops_per_eval(7) > bench.feynman_tensor_flops_per_eval(6)

@@ -209,7 +209,8 @@ def feynman_tensor_flops_per_eval(d: int) -> int:
     F(x) and U(x) (the nested form in FP64 for d = 3..6), the deformation
     y = -lam x (1 - x) g, F(z) and U(z) by the exact Taylor series (for d = 3..6 y.H y over
     the upper triangle and the cubic and quadratic parts at y by nested forms), det J by elimination
-    without pivoting (the first column on purely imaginary entries), 1 / (F^2 sqrt F) by the
+    without pivoting (the first column on purely imaginary entries; for d = 3..6 the
+    symmetric elimination of diag(1 + i Lambda) + diag(lx) i H), 1 / (F^2 sqrt F) by the
     principal root, the products with U and det J, the weight and the accumulation.  It does
     not grow with the number of monomials."""
     P = d * (d + 1) // 2
@@ -234,21 +235,41 @@ def feynman_tensor_flops_per_eval(d: int) -> int:
         mul += 2 * P
         fma += 2
         add += 1                                         # F(z), U(z)
-    mul += d * d + d                                     # Jacobian entries
-    fma += 2 * d
-    fma += 1 + (d - 1) * 2 * (d - 1)                     # first column
-    mul += 3 + (d - 1) * 2
-    special += 1
-    for c in range(1, d):                                # pivots c >= 1
-        fma += 2
-        mul += 2
-        if c + 1 < d:
-            fma += 1
-            mul += 3
-            special += 1
-            rows = d - c - 1
-            fma += rows * (2 + 4 * rows)
-            mul += rows * 2
+    if d in FEYN_FIXED_DIMS:
+        # symmetric elimination of J = diag(1 + i Lambda) + diag(lx) i H (upper triangle)
+        fma += d
+        mul += 2 * d                                     # Lambda
+        fma += 1 + 1                                     # first pivot, its reciprocal
+        mul += 3 + 2 + 2 * (d - 1)
+        special += 1
+        fma += (d - 1) * d // 2                          # first step: K' = i H + u H_0q
+        mul += (d - 1) * d // 2
+        for c in range(1, d):                            # pivots c >= 1
+            fma += 2 + 2                                 # pivot, det product
+            mul += 2
+            if c + 1 < d:
+                fma += 1
+                mul += 3 + 2
+                special += 1
+                rows = d - c - 1
+                fma += rows * 2 + 4 * rows * (rows + 1) // 2
+                mul += rows * 2
+    else:
+        mul += d * d + d                                 # Jacobian entries
+        fma += 2 * d
+        fma += 1 + (d - 1) * 2 * (d - 1)                 # first column
+        mul += 3 + (d - 1) * 2
+        special += 1
+        for c in range(1, d):                            # pivots c >= 1
+            fma += 2
+            mul += 2
+            if c + 1 < d:
+                fma += 1
+                mul += 3
+                special += 1
+                rows = d - c - 1
+                fma += rows * (2 + 4 * rows)
+                mul += rows * 2
     fma += 1                                             # principal sqrt, F^2 sqrt F, 1/den
     mul += 1 + 1 + 1
     add += 1

@@ -487,6 +487,58 @@ __device__ __forceinline__ cplx feynman_jacobian_det(const double *x, const doub
     return det;
 }
 
+// The same determinant by symmetric elimination.  J = D + P K with D = diag(1 + i Λ),
+// Λ_k = -lam (1 - 2 x_k) g_k, P = diag(lx) real and K = i H complex symmetric.
+// Eliminating column c (pivot A_cc = D_c + p_c K_cc) leaves the trailing block in the same
+// shape, D + P K' with K'_rq = K_rq - (p_c / A_cc) K_rc K_cq, still symmetric, so only the
+// upper triangle of K is updated: about two thirds of the general elimination's complex
+// updates, and J's entries p_k H_kl are never formed.  The pivots, and so det J, equal
+// those of the elimination above up to rounding.  In the first step K is purely
+// imaginary and K_rc K_cq = -H_rc H_cq is real.
+template <int D>
+__device__ __forceinline__ cplx feynman_jacobian_det_sym(const double *x, const double *lx,
+                                                         const double *g, const double *H,
+                                                         double lam) {
+    double Kr[D * D], Ki[D * D];   // upper triangle, K_rq at r * D + q for q >= r
+    double lamb[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) lamb[k] = -lam * fma(-2.0, x[k], 1.0) * g[k];
+    cplx det = {1.0, fma(lx[0], H[0], lamb[0])};   // A_00 = 1 + i (Λ_0 + p_0 H_00)
+    if constexpr (D == 1) return det;
+    {
+        const cplx inv = crecip(det);
+        const cplx c0 = {lx[0] * inv.re, lx[0] * inv.im};
+#pragma unroll
+        for (int r = 1; r < D; ++r) {
+            const cplx u = {c0.re * H[r], c0.im * H[r]};   // (p_0 / A_00) H_r0
+#pragma unroll
+            for (int q = r; q < D; ++q) {                   // K'_rq = i H_rq + u H_0q
+                Kr[r * D + q] = u.re * H[q];
+                Ki[r * D + q] = fma(u.im, H[q], H[r * D + q]);
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 1; c < D; ++c) {
+        const cplx piv = {fma(lx[c], Kr[c * D + c], 1.0), fma(lx[c], Ki[c * D + c], lamb[c])};
+        det = cmul(det, piv);
+        if (c + 1 == D) break;
+        const cplx inv = crecip(piv);
+        const cplx cc = {lx[c] * inv.re, lx[c] * inv.im};
+#pragma unroll
+        for (int r = c + 1; r < D; ++r) {
+            const cplx w = cmul(cc, {Kr[c * D + r], Ki[c * D + r]});   // (p_c / A_cc) K_rc
+#pragma unroll
+            for (int q = r; q < D; ++q) {                              // K_rq -= w K_cq
+                const double ar = Kr[c * D + q], ai = Ki[c * D + q];
+                Kr[r * D + q] = fma(-w.re, ar, fma(w.im, ai, Kr[r * D + q]));
+                Ki[r * D + q] = fma(-w.re, ai, fma(-w.im, ar, Ki[r * D + q]));
+            }
+        }
+    }
+    return det;
+}
+
 // Principal square root: Re >= 0, the sign of Im from Im a (so a = -x - 0i maps to the
 // lower side of the cut, as exp(Log(a) / 2) with the arg in (-pi, pi] and signed zeros).
 // The branch that avoids cancellation: t = sqrt((|a| + |Re a|) / 2), the other part
@@ -779,7 +831,9 @@ static __device__ __noinline__ void feynman_value_dense(const double *xin, int d
         Uz = {Ux - yU2y, gUy};
     }
     if (Fz.im > 0.0) ++signfail;
-    const cplx det = feynman_jacobian_det<DT>(x, xo, g, H, d, lam);
+    cplx det;
+    if constexpr (FX) det = feynman_jacobian_det_sym<DT>(x, xo, g, H, lam);
+    else det = feynman_jacobian_det<DT>(x, xo, g, H, d, lam);
     feynman_combine(Uz, Fz, det, ps.pa, ps.pb, re, im);
 }
 

@@ -98,7 +98,8 @@ def test_complex_family_work_split():
     high products for d = 5 (75 Hessian terms, 25 each for H x, F2 x, U2 x) on top of the
     Korobov-3 map and weight; the FP64 count keeps the nested-form values F(x) (55 fused
     multiply-adds) and U(x) (20) of that part, and the Taylor terms at y take the upper
-    triangle and the nested forms.  d = 7 keeps the all-FP64 form."""
+    triangle and the nested forms, det J the symmetric elimination.  d = 7 keeps the
+    all-FP64 form."""
     assert bench.feynman_fixed_int_mul_per_eval(5) == bench.MUL_HI * 150
     assert bench.feynman_int_mul_per_eval(("korobov", 3), 5) == (
         bench.MUL_HI * 150 + 5 * bench.korobov_map_muls(3) + bench.korobov_weight_muls(3))
@@ -109,5 +110,9 @@ def test_complex_family_work_split():
     # values 55 + 20 fma; Taylor terms 10 + 10 + 10 fma and 5 mul (y.H y, g.y, grad U.y),
     # 35 + 30 + 10 fma (nested cubic and quadratic at y), 1 fma, 2 adds
     fixed_form = 2 * (55 + 20) + 2 * (30 + 75 + 1) + 5 + 2
+    # det J: general elimination of the formed J (122 fma, 70 mul, 4 reciprocals) against
+    # the symmetric elimination of diag(1 + i Lambda) + diag(lx) i H (88 fma, 68 mul, 4)
+    fp64_form += 2 * 122 + 70 + 4
+    fixed_form += 2 * 88 + 68 + 4
     assert bench.feynman_tensor_flops_per_eval(5) == 1139 - fp64_form + fixed_form
     assert bench.feynman_tensor_flops_per_eval(7) > bench.feynman_tensor_flops_per_eval(6)

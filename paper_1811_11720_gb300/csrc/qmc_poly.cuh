@@ -51,6 +51,10 @@ struct PolyShared {
     // as round(c 2^sf) at u[3 kMaxTerms + e], U's as round(c 2^su) at u[kMaxTerms + e];
     // the nested-form coefficients of F and U after their FP64 tensors (feyn_add_horner)
     int feyn_fixed, sf, su;
+    // real family, dense F with non-negative coefficients and a positive constant term
+    // whose error bound passes (stage_poly): the dense coefficients in place as
+    // round(c 2^sfix) (unsigned), evaluated by dense_eval_fixed
+    int fixed_f, sfix;
 };
 
 // Symmetric-tensor form of the complex family (deg U <= 2, deg F <= 3, d <= kFeynDenseMaxDim):
@@ -213,6 +217,7 @@ __device__ __forceinline__ void stage_poly(const P &p, PolyShared &ps, bool allo
         ps.maxdeg_u = 0;
         ps.maxdeg_f = 0;
         ps.feyn_fixed = 0;
+        ps.fixed_f = 0;
     }
     __syncthreads();
     // keys as a cubic in d+1 variables (degree of each monomial recorded)
@@ -321,12 +326,112 @@ __device__ __forceinline__ void stage_poly(const P &p, PolyShared &ps, bool allo
                 if (keys[q] == e) acc += p.fcoef[q];
             ps.buf.v[2 * kMaxTerms + e] = acc;
         }
+        // Fixed point for F when its relative error provably stays below 2^-42: with
+        // non-negative coefficients of sum B and constant term c0 > 0, F >= c0 on the
+        // cube; s = 62 - ilogb(B) keeps every partial sum below 2^63 with 2^-s <= 2^-62 B,
+        // and N products at under 4.5 units of 2^-s each (dense_eval_fixed) give a
+        // relative error below 4.5 N (B / c0) 2^-62, required <= 2^-42.
+        __syncthreads();
+        if (tid == 0) {
+            const double *c = ps.buf.v + 2 * kMaxTerms;
+            double B = 0.0;
+            int ok = 1;
+            for (int e = 0; e < n3; ++e) {
+                ok = ok && c[e] >= 0.0;
+                B += c[e];
+            }
+            const double c0 = c[n3 - 1];   // x_d^D: the constant term
+            const int N = n3 + (use_f == 3 ? dense_size(V, 2) : 0) + V;
+            ok = ok && c0 > 0.0 && B < 1e300 && 4.5 * N * B <= 0x1p20 * c0;
+            ps.fixed_f = ok;
+            ps.sfix = ok ? 62 - ilogb(B) : 0;
+        }
+        __syncthreads();
+        if (ps.fixed_f)
+            for (int e = tid; e < n3; e += blockDim.x)
+                ps.buf.u[2 * kMaxTerms + e] =
+                    (uint64_t)llrint(ldexp(ps.buf.v[2 * kMaxTerms + e], ps.sfix));
     } else {
         for (int q = tid; q < p.nf; q += blockDim.x) {
             ps.buf.v[2 * kMaxTerms + q] = p.fcoef[q];
             ps.buf.u[3 * kMaxTerms + q] = pack_monomial(p.fexp + (size_t)q * d, d);
         }
     }
+}
+
+// Fixed point for polynomial work on the integer multiply pipe: a value v is held as the
+// integer round(v 2^s) with one scale s per polynomial (signed for the complex family's
+// tensors, unsigned for the real family's non-negative dense forms), a coordinate x in
+// [0, 1] as the uint64 X = x 2^64.
+//   c X / 2^64 for signed c: the unsigned high word of (c mod 2^64) X, minus X when c < 0.
+__device__ __forceinline__ int64_t smulhi_x(int64_t c, uint64_t X) {
+    const uint64_t h = mulhi_trunc((uint64_t)c, X);
+    return (int64_t)(c < 0 ? h - X : h);
+}
+// x in [0, 1] to x 2^64, truncated (x = 1 saturates to 2^64 - 1).  For 0 < x < 1 with
+// biased exponent E <= 1022, x 2^64 is the 64-bit mantissa shifted right by 1022 - E.
+// The range tests compare the bit pattern as a signed integer (non-negative doubles order
+// like their bits; negative ones have the sign bit set), which keeps them off the FP64 pipe.
+__device__ __forceinline__ uint64_t unit_to_fixed64(double x) {
+    const long long b = __double_as_longlong(x);
+    if (b >= 0x3FF0000000000000ll) return ~0ull;   // x >= 1
+    if (b <= 0) return 0ull;                       // x <= 0
+    const int r = 1022 - (int)(b >> 52);
+    const uint64_t m = ((uint64_t)b << 11) | 0x8000000000000000ull;
+    return r >= 64 ? 0ull : (m >> r);
+}
+// v 2^-s to double, truncated toward zero, by integer operations.
+__device__ __forceinline__ double fixed_s64_to_double(int64_t v, int s) {
+    const uint64_t sign = (uint64_t)v & 0x8000000000000000ull;
+    const uint64_t a = v < 0 ? (uint64_t)0 - (uint64_t)v : (uint64_t)v;
+    if (!a) return 0.0;
+    const int lz = __clzll(a);
+    const uint64_t m = a << lz;   // a 2^lz in [2^63, 2^64): v = m 2^(63 - lz - s) / 2^63
+    const uint64_t be1 = (uint64_t)(1085 - lz - s);   // biased exponent minus one
+    return __longlong_as_double((long long)(sign | ((be1 << 52) + (m >> 11))));
+}
+
+// Unsigned u 2^-s to double, truncated, by integer operations (u = 0 gives 0).
+__device__ __forceinline__ double fixed_u64_to_double(uint64_t u, int s) {
+    if (!u) return 0.0;
+    const int lz = __clzll(u);
+    const uint64_t m = u << lz;
+    const uint64_t be1 = (uint64_t)(1085 - lz - s);
+    return __longlong_as_double((long long)((be1 << 52) + (m >> 11)));
+}
+
+// The dense Horner form below in unsigned fixed point, for non-negative coefficients
+// C = round(c 2^s) and X[k] = x_k 2^64 (X[d] = 2^64 - 1 for the padding variable x_d = 1).
+// Every partial sum is at most the sum of the coefficients, below 2^63.  Each truncated
+// product is off by under 4 units of 2^-s (mulhi_trunc's bound, the dropped fraction and
+// X[d] < 2^64), each coefficient by half a unit.
+__device__ __forceinline__ uint64_t dense_eval_fixed(const uint64_t *X, int V, int D,
+                                                     const uint64_t *C) {
+    uint64_t F = 0;
+    int idx = 0;
+    if (D == 3) {
+#pragma unroll 1
+        for (int a = 0; a < V; ++a) {
+            uint64_t sa = 0;
+#pragma unroll 1
+            for (int b = a; b < V; ++b) {
+                uint64_t t = 0;
+#pragma unroll 1
+                for (int c = b; c < V; ++c) t += mulhi_trunc(C[idx++], X[c]);
+                sa += mulhi_trunc(X[b], t);
+            }
+            F += mulhi_trunc(X[a], sa);
+        }
+    } else {
+#pragma unroll 1
+        for (int a = 0; a < V; ++a) {
+            uint64_t t = 0;
+#pragma unroll 1
+            for (int b = a; b < V; ++b) t += mulhi_trunc(C[idx++], X[b]);
+            F += mulhi_trunc(X[a], t);
+        }
+    }
+    return F;
 }
 
 // Dense Horner evaluation at x[0..d] with x[d] = 1 (x in local memory).
@@ -397,8 +502,18 @@ __device__ __forceinline__ double sector_value(const double *xin, int d, const P
     x[d] = 1.0;
     const double U = ps.dense_u ? dense_eval(x, d + 1, ps.dense_u, ps.buf.v)
                                 : poly_real(x, ps.nu, ps.buf.v, ps.buf.u + kMaxTerms);
-    const double F = ps.dense_f ? dense_eval(x, d + 1, ps.dense_f, ps.buf.v + 2 * kMaxTerms)
-                                : poly_real(x, ps.nf, ps.buf.v + 2 * kMaxTerms, ps.buf.u + 3 * kMaxTerms);
+    double F;
+    if (ps.fixed_f) {
+        uint64_t X[kMaxDim + 1];
+#pragma unroll 1
+        for (int k = 0; k < d; ++k) X[k] = unit_to_fixed64(x[k]);
+        X[d] = ~0ull;
+        F = fixed_u64_to_double(dense_eval_fixed(X, d + 1, ps.dense_f, ps.buf.u + 2 * kMaxTerms),
+                                ps.sfix);
+    } else {
+        F = ps.dense_f ? dense_eval(x, d + 1, ps.dense_f, ps.buf.v + 2 * kMaxTerms)
+                       : poly_real(x, ps.nf, ps.buf.v + 2 * kMaxTerms, ps.buf.u + 3 * kMaxTerms);
+    }
     return pow_pos(U, ps.pa) * pow_pos(F, -ps.pb);
 }
 
@@ -589,37 +704,6 @@ __device__ __forceinline__ void feynman_combine(cplx U, cplx F, cplx det, double
     v = cmul(v, det);
     re = v.re;
     im = v.im;
-}
-
-// Signed fixed point for the tensor contractions of the symmetric-tensor form: a value v
-// is held as the int64 round(v 2^s) with one scale s per polynomial, a coordinate x in
-// [0, 1] as the uint64 X = x 2^64.  Products go through the integer multiply pipe.
-//   c X / 2^64 for signed c: the unsigned high word of (c mod 2^64) X, minus X when c < 0.
-__device__ __forceinline__ int64_t smulhi_x(int64_t c, uint64_t X) {
-    const uint64_t h = mulhi_trunc((uint64_t)c, X);
-    return (int64_t)(c < 0 ? h - X : h);
-}
-// x in [0, 1] to x 2^64, truncated (x = 1 saturates to 2^64 - 1).  For 0 < x < 1 with
-// biased exponent E <= 1022, x 2^64 is the 64-bit mantissa shifted right by 1022 - E.
-// The range tests compare the bit pattern as a signed integer (non-negative doubles order
-// like their bits; negative ones have the sign bit set), which keeps them off the FP64 pipe.
-__device__ __forceinline__ uint64_t unit_to_fixed64(double x) {
-    const long long b = __double_as_longlong(x);
-    if (b >= 0x3FF0000000000000ll) return ~0ull;   // x >= 1
-    if (b <= 0) return 0ull;                       // x <= 0
-    const int r = 1022 - (int)(b >> 52);
-    const uint64_t m = ((uint64_t)b << 11) | 0x8000000000000000ull;
-    return r >= 64 ? 0ull : (m >> r);
-}
-// v 2^-s to double, truncated toward zero, by integer operations.
-__device__ __forceinline__ double fixed_s64_to_double(int64_t v, int s) {
-    const uint64_t sign = (uint64_t)v & 0x8000000000000000ull;
-    const uint64_t a = v < 0 ? (uint64_t)0 - (uint64_t)v : (uint64_t)v;
-    if (!a) return 0.0;
-    const int lz = __clzll(a);
-    const uint64_t m = a << lz;   // a 2^lz in [2^63, 2^64): v = m 2^(63 - lz - s) / 2^63
-    const uint64_t be1 = (uint64_t)(1085 - lz - s);   // biased exponent minus one
-    return __longlong_as_double((long long)(sign | ((be1 << 52) + (m >> 11))));
 }
 
 // Hessian and gradient of F and grad U of the symmetric-tensor form at x, as

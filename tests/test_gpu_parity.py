@@ -499,6 +499,30 @@ def test_sector_real_matches_oracle(env, d, nu, nf):
     _compare(gre, None, o, n)
 
 
+@pytest.mark.parametrize("case", ["negative_term", "small_constant", "no_constant_u_only"])
+def test_sector_real_fixed_point_guard(env, case):
+    """The dense F takes fixed point only when its relative error bound holds (non-negative
+    coefficients, a constant term c0 > 0 and 4.5 N B / c0 <= 2^20); these F fail the
+    guard (a negative coefficient, c0 = 1e-5 of B) and take the FP64 form, and the third
+    keeps a qualifying F beside a U without constant term.  All match the oracle."""
+    q, torch, dev, tab = env
+    d = 6
+    fl = W.sector_like(40 + len(case), d, 60, 120)
+    cf = fl.F.coef.copy()
+    if case == "negative_term":
+        cf[0] = 2.0 + cf[1:].sum()
+        cf[5] = -0.01
+    elif case == "small_constant":
+        cf[0] = 1e-5 * cf[1:].sum()
+    fl = W.FeynmanLike(fl.U, W.Polynomial(cf, fl.F.exps), fl.a, fl.b, 0.0, d)
+    n, m = 4691, 4
+    D = O.shifts(17, m, d)
+    z = tab.z_for(n)[:d]
+    _, gre, _, _ = _gpu_sums(env, q.Integrand.polynomial(fl), n, z, D, ("korobov", 3))
+    o = O.shift_sums(O.from_feynman(fl), ("korobov", 3), n, z, D)
+    _compare(gre, None, o, n, label=f"sector guard {case}")
+
+
 def test_evaluate_matches_oracle(env):
     q, torch, dev, tab = env
     n, d = 4691, 5

@@ -401,34 +401,75 @@ __device__ __forceinline__ double fixed_u64_to_double(uint64_t u, int s) {
 }
 
 // The dense Horner form below in unsigned fixed point, for non-negative coefficients
-// C = round(c 2^s) and X[k] = x_k 2^64 (X[d] = 2^64 - 1 for the padding variable x_d = 1).
+// C = round(c 2^s) and X[k] = x_k 2^64, k < V - 1.  The padding variable x_(V-1) = 1 is
+// not multiplied: the loop iterations that meet it are peeled into plain additions.
 // Every partial sum is at most the sum of the coefficients, below 2^63.  Each truncated
-// product is off by under 4 units of 2^-s (mulhi_trunc's bound, the dropped fraction and
-// X[d] < 2^64), each coefficient by half a unit.
-__device__ __forceinline__ uint64_t dense_eval_fixed(const uint64_t *X, int V, int D,
+// product is off by under 3 units of 2^-s (mulhi_trunc's bound and the dropped
+// fraction), each coefficient by half a unit.  VT > 0: V compiled in (unrolled loops,
+// X in registers); VT = 0: V at run time.  Same operations in the same order.
+template <int VT>
+__device__ __forceinline__ uint64_t dense_eval_fixed(const uint64_t *X, int V_rt, int D,
                                                      const uint64_t *C) {
+    const int V = VT > 0 ? VT : V_rt;
     uint64_t F = 0;
     int idx = 0;
     if (D == 3) {
-#pragma unroll 1
-        for (int a = 0; a < V; ++a) {
+#pragma unroll
+        for (int a = 0; a < V - 1; ++a) {
             uint64_t sa = 0;
-#pragma unroll 1
-            for (int b = a; b < V; ++b) {
+#pragma unroll
+            for (int b = a; b < V - 1; ++b) {
                 uint64_t t = 0;
-#pragma unroll 1
-                for (int c = b; c < V; ++c) t += mulhi_trunc(C[idx++], X[c]);
+#pragma unroll
+                for (int c = b; c < V - 1; ++c) t += mulhi_trunc(C[idx++], X[c]);
+                t += C[idx++];                 // c = V - 1
                 sa += mulhi_trunc(X[b], t);
             }
+            sa += C[idx++];                    // b = c = V - 1
             F += mulhi_trunc(X[a], sa);
         }
     } else {
-#pragma unroll 1
-        for (int a = 0; a < V; ++a) {
+#pragma unroll
+        for (int a = 0; a < V - 1; ++a) {
             uint64_t t = 0;
-#pragma unroll 1
-            for (int b = a; b < V; ++b) t += mulhi_trunc(C[idx++], X[b]);
+#pragma unroll
+            for (int b = a; b < V - 1; ++b) t += mulhi_trunc(C[idx++], X[b]);
+            t += C[idx++];                     // b = V - 1
             F += mulhi_trunc(X[a], t);
+        }
+    }
+    return F + C[idx];                         // the constant term
+}
+
+// The FP64 dense Horner form with V compiled in, the x_(V-1) = 1 iterations peeled:
+// fma(c, 1, t) and fma(1, t, s) round like the additions that replace them, so the
+// result equals dense_eval's bit for bit.
+template <int V, int D>
+__device__ __forceinline__ double dense_eval_t(const double *x, const double *C) {
+    double F = 0.0;
+    int idx = 0;
+    if constexpr (D == 3) {
+#pragma unroll
+        for (int a = 0; a < V; ++a) {
+            double sa = 0.0;
+#pragma unroll
+            for (int b = a; b < V; ++b) {
+                double t = 0.0;
+#pragma unroll
+                for (int c = b; c < V - 1; ++c) t = fma(C[idx++], x[c], t);
+                t = t + C[idx++];
+                sa = b < V - 1 ? fma(x[b], t, sa) : sa + t;
+            }
+            F = a < V - 1 ? fma(x[a], sa, F) : F + sa;
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < V; ++a) {
+            double t = 0.0;
+#pragma unroll
+            for (int b = a; b < V - 1; ++b) t = fma(C[idx++], x[b], t);
+            t = t + C[idx++];
+            F = a < V - 1 ? fma(x[a], t, F) : F + t;
         }
     }
     return F;
@@ -495,7 +536,36 @@ __device__ __forceinline__ double pow_pos(double x, double y) {
     return pow(x, y);
 }
 
+// The real family with F in fixed point, both forms dense and d compiled in (d = 3..8):
+// the coordinates and the unrolled loops stay in registers.
+template <int D>
+static __device__ __noinline__ double sector_value_fixed(const double *xin, const PolyShared &ps) {
+    constexpr int V = D + 1;
+    double x[D];
+    uint64_t X[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        x[k] = xin[k];
+        X[k] = unit_to_fixed64(x[k]);
+    }
+    const double U = ps.dense_u == 3 ? dense_eval_t<V, 3>(x, ps.buf.v) : dense_eval_t<V, 2>(x, ps.buf.v);
+    const uint64_t *C = ps.buf.u + 2 * kMaxTerms;
+    const uint64_t Fq = ps.dense_f == 3 ? dense_eval_fixed<V>(X, V, 3, C) : dense_eval_fixed<V>(X, V, 2, C);
+    return pow_pos(U, ps.pa) * pow_pos(fixed_u64_to_double(Fq, ps.sfix), -ps.pb);
+}
+
 __device__ __forceinline__ double sector_value(const double *xin, int d, const PolyShared &ps) {
+    if (ps.fixed_f && ps.dense_u) {
+        switch (d) {
+        case 3: return sector_value_fixed<3>(xin, ps);
+        case 4: return sector_value_fixed<4>(xin, ps);
+        case 5: return sector_value_fixed<5>(xin, ps);
+        case 6: return sector_value_fixed<6>(xin, ps);
+        case 7: return sector_value_fixed<7>(xin, ps);
+        case 8: return sector_value_fixed<8>(xin, ps);
+        default: break;
+        }
+    }
     double x[kMaxDim + 1];
 #pragma unroll 1
     for (int k = 0; k < d; ++k) x[k] = xin[k];
@@ -504,11 +574,10 @@ __device__ __forceinline__ double sector_value(const double *xin, int d, const P
                                 : poly_real(x, ps.nu, ps.buf.v, ps.buf.u + kMaxTerms);
     double F;
     if (ps.fixed_f) {
-        uint64_t X[kMaxDim + 1];
+        uint64_t X[kMaxDim];
 #pragma unroll 1
         for (int k = 0; k < d; ++k) X[k] = unit_to_fixed64(x[k]);
-        X[d] = ~0ull;
-        F = fixed_u64_to_double(dense_eval_fixed(X, d + 1, ps.dense_f, ps.buf.u + 2 * kMaxTerms),
+        F = fixed_u64_to_double(dense_eval_fixed<0>(X, d + 1, ps.dense_f, ps.buf.u + 2 * kMaxTerms),
                                 ps.sfix);
     } else {
         F = ps.dense_f ? dense_eval(x, d + 1, ps.dense_f, ps.buf.v + 2 * kMaxTerms)

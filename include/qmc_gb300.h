@@ -93,7 +93,13 @@ enum {
  *   Genz / trig:  c[dim], w[dim]; trig also h[dim] (integer frequencies).
  *   Polynomial families: U = sum_m ucoef[m] prod_k x_k^uexp[m*dim+k] (nu terms), F likewise
  *   (nf terms), exponents 0..15; the value is U^pa F^-pb (principal branch) times, for
- *   QMC_FEYNMAN, det(dz/dx) at z_k = x_k - i lambda x_k (1 - x_k) dF/dx_k (real x). */
+ *   QMC_FEYNMAN, det(dz/dx) at z_k = x_k - i lambda x_k (1 - x_k) dF/dx_k (real x).
+ *   Arithmetic is FP64 except for two integer-pipe forms in 64-bit fixed point, chosen at
+ *   staging: QMC_SECTOR's dense F when its coefficients are non-negative with a constant
+ *   term c0 > 0 and the bound 4.5 N (sum of coefficients / c0) 2^-62 on its relative error
+ *   (N products) is at most 2^-42; QMC_FEYNMAN's Hessian, dF and dU for dim 3..6 (deg U <= 2,
+ *   deg F <= 3), each within 2^-49 of the sum of |coefficients|.  U(x), F(x) of QMC_FEYNMAN,
+ *   and everything else, stay FP64. */
 typedef struct {
     int family;
     int dim;

@@ -18,7 +18,9 @@ the fixed-order tile reduction and the shift reduction (mean and standard error)
              x evaluations per launch / CUDA-event launch time, peak = the same
              operation's rate measured on the device by qmc_probe_units; for the complex
              workload the FP64 pipe (counted FP64 flops against the measured FP64 FMA
-             rate).  The method's FP64 work rate against the FP64 peak is reported beside
+             rate), likewise for --workload sector (four real sector integrands U/F^2.5,
+             d = 8, 200 + 200 monomials: the batching configuration's kernel), each with
+             the integer pipe's share beside it.  The method's FP64 work rate against the FP64 peak is reported beside
              it as fp64_equivalent (it can exceed 1: the kernel does much of that work
              exactly on the integer pipe)
   latency, feynman, batch, serve   bounded runs of the other configurations (the d = 4
@@ -178,6 +180,46 @@ def feynman_flops_per_eval(fl) -> int:
     return derivs + complex_vals + deform + lu + 2 * 9 + 12 + 4
 
 
+def sector_flops_per_eval(fl, transform) -> int:
+    """Algorithmic FP64 work of one evaluation of the real sector integrand U^a F^-b in the
+    paper's term-by-term form (rules of fp64_flops_per_eval): per monomial of degree q,
+    q - 1 multiplies and one fused multiply-add; the power F^-b (a = 1, half-integer b:
+    two multiplies, a square root and a reciprocal) and the product with U; the Korobov-r
+    map per dimension, the weight and the accumulation as for the Genz families."""
+    terms = fl.U.nterms + fl.F.nterms
+    factors = int(fl.U.exps.sum() + fl.F.exps.sum())
+    d = fl.d
+    r = transform[1] if transform[0] == "korobov" else 0
+    tr = d * (2 * (2 * r + 1) + (r + 2) + 1) if r else 0
+    return (factors - terms) + 2 * terms + 5 + tr + 2 + 2 * d
+
+
+def sector_kernel_flops_per_eval(d: int) -> int:
+    """FP64 work of one evaluation in the form the kernel runs for the sector benchmark
+    workload (both polynomials dense, F in fixed point, d compiled in; qmc_poly.cuh): U's
+    dense quadratic in V = d + 1 variables with the x_d = 1 iterations as additions
+    (V (V - 1) / 2 + V - 1 fma, V + 1 adds), the power U / (F^2 sqrt F) (3 mul, sqrt,
+    reciprocal), the weight (2 mul) and the accumulation (2 adds).  F's Horner form and the
+    Korobov map run on the integer pipe (sector_int_mul_per_eval)."""
+    V = d + 1
+    fma = V * (V - 1) // 2 + V - 1
+    return 2 * fma + (V + 1) + 5 + 2 + 2
+
+
+def sector_int_mul_per_eval(transform, d: int) -> int:
+    """32-bit multiplies of one sector evaluation on the integer pipe: F's dense cubic in
+    fixed point with the x_d = 1 iterations as additions (C(V+1, 3) + V (V - 1) / 2 + V - 1
+    truncated high products, V = d + 1) and the integer Korobov<r,r> map and weight."""
+    V = d + 1
+    prods = math.comb(V + 1, 3) + V * (V - 1) // 2 + (V - 1)
+    per = MUL_HI * prods
+    kind = transform[0]
+    r = transform[1] if kind == "korobov" else 0
+    if kind == "korobov" and 1 <= r <= 6 and (len(transform) < 3 or transform[2] == r):
+        per += korobov_map_muls(r) * d + korobov_weight_muls(r)
+    return per
+
+
 FEYN_FIXED_DIMS = range(3, 7)      # dimensions whose contractions run in fixed point
 
 
@@ -292,6 +334,9 @@ def parse_transform(tok: str):
 
 FEYNMAN_FAMILY = 20
 FEYNMAN_INTEGRALS = 4
+SECTOR_FAMILY = 21
+SECTOR_INTEGRALS = 4
+SECTOR_D, SECTOR_TERMS = 8, 200
 
 
 def workload_items(rank: int = 0, only: str | None = None, workload: str = "genz"):
@@ -302,6 +347,12 @@ def workload_items(rank: int = 0, only: str | None = None, workload: str = "genz
     if workload == "feynman":
         return [(FEYNMAN_FAMILY, 5, ("korobov", 3), W.feynman_regular(1000 + 17 * rank + k), None)
                 for k in range(FEYNMAN_INTEGRALS)]
+    if workload == "sector":
+        # real sector integrands U / F^2.5, d = 8, 200 + 200 monomials (both forms dense,
+        # F in fixed point): the lattice-sum kernel of the batching configuration
+        return [(SECTOR_FAMILY, SECTOR_D, ("korobov", 3),
+                 W.sector_like(1000 + 17 * rank + k, SECTOR_D, SECTOR_TERMS, SECTOR_TERMS), None)
+                for k in range(SECTOR_INTEGRALS)]
     if workload == "feynman_like":
         # the configuration's literal polynomials (all 15 + 35 monomials, coefficients
         # U(-1, 2), lam = 0.5): the same kernel cost; U F^-2.5 is not integrable where F
@@ -450,7 +501,8 @@ def run_gpu(args, rank: int, world: int):
     prepared = []
     max_ws = 0
     for idx, (fam, d, tr, c, w) in enumerate(items):
-        f = q.Integrand.polynomial(c) if fam == FEYNMAN_FAMILY else q.Integrand.genz(fam, c, w)
+        f = (q.Integrand.polynomial(c) if fam in (FEYNMAN_FAMILY, SECTOR_FAMILY)
+             else q.Integrand.genz(fam, c, w))
         D = q.make_shifts(args.seed + 7919 * rank + idx, M_SHIFTS, d)
         Dd = torch.from_numpy(D.astype(np.int64)).to(dev)
         r = q.rule(n, zfull[:d], Dd, tr)
@@ -464,10 +516,14 @@ def run_gpu(args, rank: int, world: int):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
     evals_per_step = len(items) * n * M_SHIFTS
     flops_per_step = sum(feynman_flops_per_eval(c) if fam == FEYNMAN_FAMILY else
+                         sector_flops_per_eval(c, tr) if fam == SECTOR_FAMILY else
                          fp64_flops_per_eval(fam, tr, d) for fam, d, tr, c, _ in items) * n * M_SHIFTS
     muls_per_step = sum(feynman_int_mul_per_eval(tr, d) if fam == FEYNMAN_FAMILY else
+                        sector_int_mul_per_eval(tr, d) if fam == SECTOR_FAMILY else
                         int_mul_per_eval(fam, tr, d, c) for fam, d, tr, c, _ in items) * n * M_SHIFTS
-    tensor_flops_per_step = sum(feynman_tensor_flops_per_eval(d) if fam == FEYNMAN_FAMILY else 0
+    # FP64 work of the form the kernel runs (polynomial families)
+    tensor_flops_per_step = sum(feynman_tensor_flops_per_eval(d) if fam == FEYNMAN_FAMILY else
+                                sector_kernel_flops_per_eval(d) if fam == SECTOR_FAMILY else 0
                                 for fam, d, tr, c, _ in items) * n * M_SHIFTS
 
     ev_k = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -549,7 +605,7 @@ def run_gpu(args, rank: int, world: int):
         for (fam, d, tr, f, fd, r, Dd, D), (_, _, _, c, w) in zip(prepared, items):
             out = q.integrate(f, table, n, M_SHIFTS, tr, seed=args.seed + 7919 * rank, stream=stream)
             if it == 0:
-                h2d += M_SHIFTS * d * 8 + (c.nbytes + w.nbytes if fam != FEYNMAN_FAMILY else
+                h2d += M_SHIFTS * d * 8 + (c.nbytes + w.nbytes if fam not in (FEYNMAN_FAMILY, SECTOR_FAMILY) else
                                            sum(a.nbytes for a in (c.U.coef, c.U.exps, c.F.coef, c.F.exps)))
         torch.cuda.synchronize(dev)
         if it > 0:                         # first pass warms the library's arena
@@ -916,6 +972,8 @@ def cpu_baseline(budget_s: float, items, nthreads: int | None = None):
     nthreads = nthreads or os.cpu_count()
     # calibrate the prefix length on the first item, then give every item the same share
     def integrand(fam, c, w):
+        if fam == SECTOR_FAMILY:
+            return O.from_feynman(c)
         return O.feynman_complex(c) if fam == FEYNMAN_FAMILY else O.genz(fam, c, w)
 
     fam, d, tr, c, w = items[0]
@@ -954,6 +1012,22 @@ def roofline(r, workload: str):
     common = {"traffic": TRAFFIC_BYTES_PER_LAUNCH if workload == "genz" else None,
               "kernel": "sums_kernel (+ tile reduction, <0.1%)",
               "per_launch_ms": round(r["kernel_ms_per_launch"], 4), "peaks": pk}
+    if workload == "sector":
+        # F's Horner form runs on the integer pipe; U, the power, weight and accumulation
+        # keep the FP64 pipe the busier unit
+        kf = r["tensor_flops_per_step"] / launches / sec / 1e9
+        fp64["note"] = ("term-by-term FP64 work of U and F (sector_flops_per_eval) against "
+                        "the measured FP64 FMA rate")
+        muls = r["muls_per_step"] / launches / sec / 1e9
+        int_pipe = {"achieved": round(muls, 1), "peak": round(pk["int_mul_gops"], 1),
+                    "unit": "G int32 mul/s", "frac": round(muls / pk["int_mul_gops"], 4),
+                    "work": "sector_int_mul_per_eval: F's fixed-point Horner form, integer "
+                            "Korobov map and weight"}
+        return {"bound": "alu", "unit": "GFLOP/s", "achieved": round(kf, 1),
+                "peak": round(pk["fp64_gflops"], 1), "frac": round(kf / pk["fp64_gflops"], 4),
+                "peak_source": "measured FP64 FMA rate (qmc_probe_units), 2 flops per FMA",
+                "work": "sector_kernel_flops_per_eval: the FP64 part of the kernel's form",
+                "int_pipe": int_pipe, "fp64_equivalent": fp64, **common}
     if workload == "feynman":
         # the FP64 pipe bounds the complex family: the symmetric-tensor form's FP64 work
         # against the measured FMA rate; the term-by-term count of the polynomials is the
@@ -1077,7 +1151,8 @@ def main():
     ap.add_argument("--only", default=None, help="FAMILY:D:TRANSFORM, e.g. 4:10:korobov3")
     ap.add_argument("--n", type=int, default=N_LATTICE, help="lattice size (a table size)")
     ap.add_argument("--workload", default="genz",
-                    choices=["genz", "feynman", "feynman_like", "batch", "serve", "latency"])
+                    choices=["genz", "feynman", "feynman_like", "sector", "batch", "serve",
+                             "latency"])
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--rates", type=float, nargs="*", default=None,
                     help="arrival rates per second (default: 2 8 32 for the Feynman profile, "
@@ -1117,6 +1192,8 @@ def main():
             "config": {"workload": (f"{'feynman_regular' if args.workload == 'feynman' else 'feynman_like'}"
                                     f"_d5_complex_korobov3_n{args.n}_m32"
                                     if args.workload in ("feynman", "feynman_like") else
+                                    f"sector_like_d{SECTOR_D}_terms{SECTOR_TERMS}_korobov3_n{args.n}_m32"
+                                    if args.workload == "sector" else
                                     f"genz_osc_corner_gauss_d6_8_10_baker_korobov1-4_n{args.n}_m32"
                                     if not args.only else f"genz_{args.only}_n{args.n}_m32"),
                        "integrals_per_step": len(workload_items(0, args.only, args.workload)),

@@ -55,6 +55,9 @@ struct PolyShared {
     // whose error bound passes (stage_poly): the dense coefficients in place as
     // round(c 2^sfix) (unsigned), evaluated by dense_eval_fixed
     int fixed_f, sfix;
+    // a = 1 and b = n + 1/2 (0 <= n <= 15): n, so that U^a F^-b = U / (F^n sqrt F) needs no
+    // per-evaluation tests of the exponents; -1 otherwise
+    int pow_half;
 };
 
 // Symmetric-tensor form of the complex family (deg U <= 2, deg F <= 3, d <= kFeynDenseMaxDim):
@@ -218,6 +221,9 @@ __device__ __forceinline__ void stage_poly(const P &p, PolyShared &ps, bool allo
         ps.maxdeg_f = 0;
         ps.feyn_fixed = 0;
         ps.fixed_f = 0;
+        const double tb = 2.0 * p.pb;
+        ps.pow_half = (p.pa == 1.0 && tb >= 1.0 && tb <= 31.0 && tb == floor(tb) &&
+                       ((int)tb & 1)) ? (int)tb / 2 : -1;
     }
     __syncthreads();
     // keys as a cubic in d+1 variables (degree of each monomial recorded)
@@ -536,11 +542,32 @@ __device__ __forceinline__ double pow_pos(double x, double y) {
     return pow(x, y);
 }
 
+// U^a F^-b of the real family: U / (F^n sqrt F) when a = 1, b = n + 1/2 and F > 0 (the
+// same products, square root and one division as pow_pos, without its tests on a and b),
+// else pow_pos.
+__device__ __forceinline__ double sector_power(double U, double F, const PolyShared &ps) {
+    if (ps.pow_half >= 0 && F > 0.0) {
+        double v = sqrt(F);
+        if (ps.pow_half) v *= ipow_u(F, ps.pow_half);
+        return U / v;
+    }
+    return pow_pos(U, ps.pa) * pow_pos(F, -ps.pb);
+}
+
 // The real family with F in fixed point, both forms dense and d compiled in (d = 3..8):
-// the coordinates and the unrolled loops stay in registers.
+// the coordinates and the unrolled loops stay in registers.  x (doubles, for U) and X
+// (x 2^64, for F) hold the same point.
+template <int D>
+__device__ __forceinline__ double sector_fixed_core(const double *x, const uint64_t *X,
+                                                    const PolyShared &ps) {
+    constexpr int V = D + 1;
+    const double U = ps.dense_u == 3 ? dense_eval_t<V, 3>(x, ps.buf.v) : dense_eval_t<V, 2>(x, ps.buf.v);
+    const uint64_t *C = ps.buf.u + 2 * kMaxTerms;
+    const uint64_t Fq = ps.dense_f == 3 ? dense_eval_fixed<V>(X, V, 3, C) : dense_eval_fixed<V>(X, V, 2, C);
+    return sector_power(U, fixed_u64_to_double(Fq, ps.sfix), ps);   // F >= c0 > 0
+}
 template <int D>
 static __device__ __noinline__ double sector_value_fixed(const double *xin, const PolyShared &ps) {
-    constexpr int V = D + 1;
     double x[D];
     uint64_t X[D];
 #pragma unroll
@@ -548,14 +575,40 @@ static __device__ __noinline__ double sector_value_fixed(const double *xin, cons
         x[k] = xin[k];
         X[k] = unit_to_fixed64(x[k]);
     }
-    const double U = ps.dense_u == 3 ? dense_eval_t<V, 3>(x, ps.buf.v) : dense_eval_t<V, 2>(x, ps.buf.v);
-    const uint64_t *C = ps.buf.u + 2 * kMaxTerms;
-    const uint64_t Fq = ps.dense_f == 3 ? dense_eval_fixed<V>(X, V, 3, C) : dense_eval_fixed<V>(X, V, 2, C);
-    return pow_pos(U, ps.pa) * pow_pos(fixed_u64_to_double(Fq, ps.sfix), -ps.pb);
+    return sector_fixed_core<D>(x, X, ps);
+}
+// The same from the coordinates in 0.64 fixed point (the integer-pipe transforms), x
+// from X by integer operations (truncated).
+template <int D>
+static __device__ __noinline__ double sector_value_fixed_x(const uint64_t *Xin, const PolyShared &ps) {
+    double x[D];
+    uint64_t X[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        X[k] = Xin[k];
+        x[k] = fixed_u64_to_double(X[k], 64);
+    }
+    return sector_fixed_core<D>(x, X, ps);
+}
+
+// Whether sector_value_fixed(_x) serves this integrand (uniform over the block).
+__device__ __forceinline__ bool sector_fixed_ok(const PolyShared &ps, int d) {
+    return ps.fixed_f && ps.dense_u && d >= 3 && d <= 8;
+}
+
+__device__ __forceinline__ double sector_value_x(const uint64_t *X, int d, const PolyShared &ps) {
+    switch (d) {
+    case 3: return sector_value_fixed_x<3>(X, ps);
+    case 4: return sector_value_fixed_x<4>(X, ps);
+    case 5: return sector_value_fixed_x<5>(X, ps);
+    case 6: return sector_value_fixed_x<6>(X, ps);
+    case 7: return sector_value_fixed_x<7>(X, ps);
+    default: return sector_value_fixed_x<8>(X, ps);
+    }
 }
 
 __device__ __forceinline__ double sector_value(const double *xin, int d, const PolyShared &ps) {
-    if (ps.fixed_f && ps.dense_u) {
+    if (sector_fixed_ok(ps, d)) {
         switch (d) {
         case 3: return sector_value_fixed<3>(xin, ps);
         case 4: return sector_value_fixed<4>(xin, ps);
@@ -583,7 +636,7 @@ __device__ __forceinline__ double sector_value(const double *xin, int d, const P
         F = ps.dense_f ? dense_eval(x, d + 1, ps.dense_f, ps.buf.v + 2 * kMaxTerms)
                        : poly_real(x, ps.nf, ps.buf.v + 2 * kMaxTerms, ps.buf.u + 3 * kMaxTerms);
     }
-    return pow_pos(U, ps.pa) * pow_pos(F, -ps.pb);
+    return sector_power(U, F, ps);
 }
 
 // ---- complex helpers --------------------------------------------------------------------

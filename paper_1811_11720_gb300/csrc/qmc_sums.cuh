@@ -112,6 +112,19 @@ __device__ __forceinline__ void eval_point(const P &p, const FamilyShared &fsh, 
             return;
         }
     }
+    if constexpr (kFixedTransform<TK> && FAM == QMC_SECTOR) {
+        // the real family with F in fixed point takes the coordinates as x 2^64 from the
+        // integer-pipe transform (no fit map)
+        if (!use_fit && sector_fixed_ok(fsh.poly, p.d)) {
+            uint64_t X[8];
+#pragma unroll 1
+            for (int j = 0; j < p.d; ++j) X[j] = transform_fixed<TK, R>(fhi(j) + dsh(j), W);
+            const double wt = weight_finish<TK, R>(W, p.t, cd);
+            g_re = sector_value_x(X, p.d, fsh.poly) * wt;
+            g_im = 0.0;
+            return;
+        }
+    }
     fa.init(fsh);
 #pragma unroll 1
     for (int j = 0; j < p.d; ++j) {

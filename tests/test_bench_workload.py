@@ -116,3 +116,30 @@ def test_complex_family_work_split():
     fixed_form += 2 * 88 + 68 + 4
     assert bench.feynman_tensor_flops_per_eval(5) == 1139 - fp64_form + fixed_form
     assert bench.feynman_tensor_flops_per_eval(7) > bench.feynman_tensor_flops_per_eval(6)
+
+
+def test_sector_work_counts():
+    """The sector kernel's integer work equals the products of the fixed-point Horner loop
+    (x_d = 1 iterations taken as additions), counted here by walking that loop, plus the
+    Korobov-3 map and weight; its FP64 work is U's dense quadratic walked the same way,
+    the power, weight and accumulation."""
+    for d in range(3, 9):
+        V = d + 1
+        prods = 0
+        for a in range(V - 1):
+            for b in range(a, V - 1):
+                prods += (V - 1) - b          # c = b .. V - 2
+                prods += 1                    # sa += X_b t
+            prods += 1                        # F += X_a sa
+        assert bench.sector_int_mul_per_eval(("korobov", 3), d) == (
+            bench.MUL_HI * prods + d * bench.korobov_map_muls(3) + bench.korobov_weight_muls(3))
+        fma = adds = 0
+        for a in range(V):
+            fma += (V - 1) - a                # b = a .. V - 2
+            adds += 1                         # t + C (b = V - 1)
+            if a < V - 1:
+                fma += 1
+            else:
+                adds += 1
+        assert bench.sector_kernel_flops_per_eval(d) == 2 * fma + adds + 5 + 2 + 2
+    assert len(bench.workload_items(0, None, "sector")) == bench.SECTOR_INTEGRALS

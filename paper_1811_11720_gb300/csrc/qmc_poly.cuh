@@ -18,6 +18,7 @@
 // det J is the product of the pivots.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 
 #include "qmc_fixed.cuh"
 #include "qmc_fp.cuh"
@@ -842,18 +843,15 @@ __device__ __forceinline__ void feynman_combine(cplx U, cplx F, cplx det, double
 // -b.  They stay in FP64, by the nested form of the monomial list
 // (c0 + sum_i x_i (c1_i + sum_{j >= i} x_j (c2_ij + sum_{k >= j} c3_ijk x_k))).
 template <int D>
-__device__ __forceinline__ void feyn_fixed_parts(const double *x, const PolyShared &ps,
-                                                 double *H, double *g, double *gU,
-                                                 double &Fx, double &Ux) {
+__device__ __forceinline__ void feyn_fixed_parts(const double *x, const uint64_t *X,
+                                                 const PolyShared &ps, double *H, double *g,
+                                                 double *gU, double &Fx, double &Ux) {
     constexpr int nU = 1 + D + D * D, nF = nU + D * D * (D + 1) / 2;
     const int64_t *ff = reinterpret_cast<const int64_t *>(ps.buf.u + 3 * kMaxTerms);
     const int64_t *uf = reinterpret_cast<const int64_t *>(ps.buf.u + kMaxTerms);
     const int64_t *f1 = ff + 1, *F2 = ff + 1 + D, *F3 = ff + 1 + D + D * D;
     const int64_t *u1 = uf + 1, *U2 = uf + 1 + D;
     const int sf = ps.sf, su = ps.su;
-    uint64_t X[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) X[k] = unit_to_fixed64(x[k]);
     int64_t Hq[D * D];
 #pragma unroll
     for (int i = 0; i < D; ++i)
@@ -919,8 +917,10 @@ __device__ __forceinline__ void feyn_fixed_parts(const double *x, const PolyShar
 //   U(z) = U(x) - y.U2 y + i grad U.y,  grad U = u1 + 2 U2 x.
 // DT > 0: the dimension as a compile-time constant (unrolled loops, per-thread arrays of
 // d entries that can stay in registers); DT = 0: d at run time.  Same operations, same order.
-template <int DT, bool FX = false>
-static __device__ __noinline__ void feynman_value_dense(const double *xin, int d_rt,
+// IN = uint64_t (with FX): the coordinates arrive as x 2^64 from the integer-pipe map and
+// the doubles are formed from them by integer operations.
+template <int DT, bool FX = false, class IN = double>
+static __device__ __noinline__ void feynman_value_dense(const IN *xin, int d_rt,
                                                         const PolyShared &ps, double &re,
                                                         double &im,
                                                         unsigned long long &signfail) {
@@ -932,14 +932,25 @@ static __device__ __noinline__ void feynman_value_dense(const double *xin, int d
     const double *f1 = fb + 1, *F2 = fb + 1 + d, *F3 = fb + 1 + d + d * d;   // F3: 6 F3
     double x[DA], g[DA], y[DA], xo[DA];
     double H[DA * DA];
-#pragma unroll
-    for (int k = 0; k < d; ++k) x[k] = xin[k];
     double Fx = 0.0, Ux = 0.0;
     double gU[DA];
     if constexpr (FX) {
         static_assert(DT > 0 && DT <= kFeynFixedMaxDim, "fixed point needs a compiled dimension");
-        feyn_fixed_parts<DT>(x, ps, H, g, gU, Fx, Ux);
+        uint64_t X[DA];
+#pragma unroll
+        for (int k = 0; k < d; ++k) {
+            if constexpr (std::is_same<IN, uint64_t>::value) {
+                X[k] = xin[k];
+                x[k] = fixed_u64_to_double(X[k], 64);
+            } else {
+                x[k] = xin[k];
+                X[k] = unit_to_fixed64(x[k]);
+            }
+        }
+        feyn_fixed_parts<DT>(x, X, ps, H, g, gU, Fx, Ux);
     } else {
+#pragma unroll
+        for (int k = 0; k < d; ++k) x[k] = xin[k];
         // Hessian of F (symmetric)
 #pragma unroll
         for (int i = 0; i < d; ++i)
@@ -1041,6 +1052,23 @@ static __device__ __noinline__ void feynman_value_dense(const double *xin, int d
     if constexpr (FX) det = feynman_jacobian_det_sym<DT>(x, xo, g, H, lam);
     else det = feynman_jacobian_det<DT>(x, xo, g, H, d, lam);
     feynman_combine(Uz, Fz, det, ps.pa, ps.pb, re, im);
+}
+
+// Whether the fixed-point form serves this integrand with coordinates given as x 2^64
+// (uniform over the block).
+__device__ __forceinline__ bool feyn_fixed_ok(const PolyShared &ps, int d) {
+    return ps.feyn_dense && ps.feyn_fixed && d >= 3 && d <= kFeynFixedMaxDim;
+}
+
+__device__ __forceinline__ void feynman_value_x(const uint64_t *X, int d, const PolyShared &ps,
+                                                double &re, double &im,
+                                                unsigned long long &signfail) {
+    switch (d) {
+    case 3: feynman_value_dense<3, true>(X, d, ps, re, im, signfail); return;
+    case 4: feynman_value_dense<4, true>(X, d, ps, re, im, signfail); return;
+    case 5: feynman_value_dense<5, true>(X, d, ps, re, im, signfail); return;
+    default: feynman_value_dense<6, true>(X, d, ps, re, im, signfail); return;
+    }
 }
 
 static __device__ __noinline__ void feynman_value(const double *xin, int d, const PolyShared &ps,

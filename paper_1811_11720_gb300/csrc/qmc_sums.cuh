@@ -125,6 +125,19 @@ __device__ __forceinline__ void eval_point(const P &p, const FamilyShared &fsh, 
             return;
         }
     }
+    if constexpr (kFixedTransform<TK> && FAM == QMC_FEYNMAN) {
+        // the complex family's fixed-point form likewise takes x 2^64 from the map
+        if (!use_fit && feyn_fixed_ok(fsh.poly, p.d)) {
+            uint64_t X[kFeynFixedMaxDim];
+#pragma unroll 1
+            for (int j = 0; j < p.d; ++j) X[j] = transform_fixed<TK, R>(fhi(j) + dsh(j), W);
+            const double wt = weight_finish<TK, R>(W, p.t, cd);
+            feynman_value_x(X, p.d, fsh.poly, g_re, g_im, signfail);
+            g_re *= wt;
+            g_im *= wt;
+            return;
+        }
+    }
     fa.init(fsh);
 #pragma unroll 1
     for (int j = 0; j < p.d; ++j) {

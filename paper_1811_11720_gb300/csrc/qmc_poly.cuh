@@ -799,12 +799,12 @@ __device__ __forceinline__ cplx csqrt_principal(cplx a) {
 // For a = 1 and a half-integer b = n + 1/2 <= 8, F^-b = 1 / (F^n sqrt(F)) with the principal
 // root, the same branch as exp(-b Log F): two square roots and a reciprocal instead of a
 // logarithm, an arctangent, an exponential and a sine/cosine pair.
+// pow_half = n >= 0 when a = 1 and b = n + 1/2 (decided once at staging).
 __device__ __forceinline__ void feynman_combine(cplx U, cplx F, cplx det, double pa, double pb,
-                                                double &re, double &im) {
-    const double twob = 2.0 * pb;
-    if (pa == 1.0 && pb > 0.0 && pb <= 8.0 && twob == floor(twob) && fmod(twob, 2.0) == 1.0) {
+                                                int pow_half, double &re, double &im) {
+    if (pow_half >= 0) {
         cplx den = csqrt_principal(F);
-        const int nint = (int)(pb - 0.5);
+        const int nint = pow_half;
 #pragma unroll 1
         for (int q = 0; q < nint; ++q) den = cmul(den, F);
         cplx v = cmul(cmul(U, crecip(den)), det);
@@ -1051,7 +1051,7 @@ static __device__ __noinline__ void feynman_value_dense(const IN *xin, int d_rt,
     cplx det;
     if constexpr (FX) det = feynman_jacobian_det_sym<DT>(x, xo, g, H, lam);
     else det = feynman_jacobian_det<DT>(x, xo, g, H, d, lam);
-    feynman_combine(Uz, Fz, det, ps.pa, ps.pb, re, im);
+    feynman_combine(Uz, Fz, det, ps.pa, ps.pb, ps.pow_half, re, im);
 }
 
 // Whether the fixed-point form serves this integrand with coordinates given as x 2^64
@@ -1163,7 +1163,7 @@ static __device__ __noinline__ void feynman_value(const double *xin, int d, cons
     if (F.im > 0.0) ++signfail;
     // J_kl = delta_kl - i lam [delta_kl (1 - 2 x_k) dF_k + x_k (1 - x_k) d2F_kl]
     const cplx det = feynman_jacobian_det<0>(x, xo, grad, H, d, lam);
-    feynman_combine(U, F, det, ps.pa, ps.pb, re, im);
+    feynman_combine(U, F, det, ps.pa, ps.pb, ps.pow_half, re, im);
 }
 
 }  // namespace qmc

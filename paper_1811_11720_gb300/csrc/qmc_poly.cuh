@@ -796,10 +796,10 @@ __device__ __forceinline__ cplx csqrt_principal(cplx a) {
 }
 
 // U^a F^-b det for principal branches: exp(a Log U - b Log F) det (a = 1: U exp(-b Log F)).
-// For a = 1 and a half-integer b = n + 1/2 <= 8, F^-b = 1 / (F^n sqrt(F)) with the principal
-// root, the same branch as exp(-b Log F): two square roots and a reciprocal instead of a
-// logarithm, an arctangent, an exponential and a sine/cosine pair.
-// pow_half = n >= 0 when a = 1 and b = n + 1/2 (decided once at staging).
+// For a = 1 and a half-integer b = n + 1/2 (pow_half = n, 0 <= n <= 15, decided once at
+// staging), F^-b = 1 / (F^n sqrt(F)) with the principal root, the same branch as
+// exp(-b Log F): two square roots and a reciprocal instead of a logarithm, an arctangent,
+// an exponential and a sine/cosine pair.
 __device__ __forceinline__ void feynman_combine(cplx U, cplx F, cplx det, double pa, double pb,
                                                 int pow_half, double &re, double &im) {
     if (pow_half >= 0) {

@@ -53,6 +53,8 @@ __device__ __forceinline__ void prepare_fit(const double *fit, int d, double *s_
         o[6] = 1.0 - a2 - a3 - a[4] - a[5];
         o[7] = o[2] * a[0];
         o[8] = o[3] * a[1];
+        o[9] = 2.0 * o[5];
+        o[10] = 3.0 * o[6];
     }
 }
 
@@ -142,7 +144,11 @@ __device__ __forceinline__ void eval_point(const P &p, const FamilyShared &fsh, 
 #pragma unroll 1
     for (int j = 0; j < p.d; ++j) {
         Mapped mx;
-        if constexpr (TK == kTKorobovInt) {
+        if constexpr (TK == kTKorobovInt && (FAM == QMC_SECTOR || FAM == QMC_FEYNMAN)) {
+            // the polynomial families use x itself: formed from x 2^64 by integer
+            // operations instead of an FP64 conversion and reflection
+            mx = Mapped{fixed_u64_to_double(transform_fixed<TK, R>(fhi(j) + dsh(j), W), 64), false};
+        } else if constexpr (TK == kTKorobovInt) {
             mx = korobov_int_x<R>(fhi(j) + dsh(j), W);
         } else {
             const double u = fixed_to_double(fhi(j) + dsh(j), flo(j), rem(j), p.n);

@@ -134,8 +134,9 @@ __device__ __forceinline__ double weight_finish(const Weight &W, const Transform
 // PolySingular map p(x) and p'(x) (Eq. (ISfit) with |a2|, |a3| as in App. A.5).  fp holds
 // per-dimension constants prepared in shared memory:
 //   [0] a0, [1] a1, [2] |a2| (a0 - 1), [3] |a3| (a1 - 1), [4] a4, [5] a5,
-//   [6] a6 = 1 - |a2| - |a3| - a4 - a5, [7] |a2| (a0 - 1) a0, [8] |a3| (a1 - 1) a1.
-constexpr int kFitStride = 9;
+//   [6] a6 = 1 - |a2| - |a3| - a4 - a5, [7] |a2| (a0 - 1) a0, [8] |a3| (a1 - 1) a1,
+//   [9] 2 a5, [10] 3 a6 (the derivative's coefficients).
+constexpr int kFitStride = 11;
 
 __device__ __forceinline__ double apply_fit(double x, const double *fp, double &jac) {
     const double d0 = fp[0] - x;
@@ -145,7 +146,7 @@ __device__ __forceinline__ double apply_fit(double x, const double *fp, double &
     const double r1 = d0 * inv;   // 1 / (a1 - x)
     const double poly = fma(fma(fp[6], x, fp[5]), x, fp[4]);
     const double p = x * fma(fp[2], r0, fma(fp[3], r1, poly));
-    const double dpoly = fma(fma(3.0 * fp[6], x, 2.0 * fp[5]), x, fp[4]);
+    const double dpoly = fma(fma(fp[10], x, fp[9]), x, fp[4]);
     const double dp = fma(fp[7] * r0, r0, fma(fp[8] * r1, r1, dpoly));
     jac *= dp;
     return p;

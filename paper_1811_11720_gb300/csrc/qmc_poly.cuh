@@ -783,15 +783,20 @@ __device__ __forceinline__ cplx feynman_jacobian_det_sym(const double *x, const 
 // Im a / (2 t).
 __device__ __forceinline__ cplx csqrt_principal(cplx a) {
     // |a| without the library's rescaling where the squares can neither overflow nor
-    // underflow (|re|, |im| in [2^-500, 2^500]; relative error within 1.5 ulp)
-    const double m = fmax(fabs(a.re), fabs(a.im));
-    const double r = (m < 0x1p500 && fmin(fabs(a.re), fabs(a.im)) > 0x1p-500)
+    // underflow (both exponents within (2^-500, 2^500): a test on the bit patterns, off the
+    // FP64 pipe; relative error within 1.5 ulp)
+    const uint64_t br = (uint64_t)__double_as_longlong(a.re), bi = (uint64_t)__double_as_longlong(a.im);
+    const uint32_t er = (uint32_t)(br >> 52) & 0x7FFu, ei = (uint32_t)(bi >> 52) & 0x7FFu;
+    const double r = (er - 524u < 998u && ei - 524u < 998u)   // 524 <= E <= 1521
                          ? sqrt(fma(a.re, a.re, a.im * a.im))
                          : hypot(a.re, a.im);
-    if (r == 0.0) return {0.0, a.im};
-    const double t = sqrt(0.5 * (r + fabs(a.re)));
-    const double o = a.im / (2.0 * t);
-    if (a.re >= 0.0) return {t, o};
+    if (((br | bi) << 1) == 0) return {0.0, a.im};            // a = 0
+    // t = sqrt(s) and a.im / (2 t) from one reciprocal square root
+    const double s = 0.5 * (r + fabs(a.re));
+    const double q = rsqrt(s);
+    const double t = s * q;
+    const double o = a.im * (0.5 * q);
+    if (!(br >> 63) || !(br << 1)) return {t, o};             // a.re >= 0 (and -0)
     return {fabs(o), copysign(t, a.im)};
 }
 
@@ -934,9 +939,9 @@ static __device__ __noinline__ void feynman_value_dense(const IN *xin, int d_rt,
     double H[DA * DA];
     double Fx = 0.0, Ux = 0.0;
     double gU[DA];
+    uint64_t X[DA];   // x 2^64 (fixed-point form only)
     if constexpr (FX) {
         static_assert(DT > 0 && DT <= kFeynFixedMaxDim, "fixed point needs a compiled dimension");
-        uint64_t X[DA];
 #pragma unroll
         for (int k = 0; k < d; ++k) {
             if constexpr (std::is_same<IN, uint64_t>::value) {
@@ -986,7 +991,10 @@ static __device__ __noinline__ void feynman_value_dense(const IN *xin, int d_rt,
     const double lam = ps.lam;
 #pragma unroll
     for (int k = 0; k < d; ++k) {
-        xo[k] = -lam * (x[k] * (1.0 - x[k]));
+        if constexpr (FX)   // x (1 - x) 2^64 as the truncated high product X (2^64 - 1 - X)
+            xo[k] = -lam * fixed_u64_to_double(mulhi_trunc(X[k], ~X[k]), 64);
+        else
+            xo[k] = -lam * (x[k] * (1.0 - x[k]));
         y[k] = xo[k] * g[k];
     }
     // F(z), U(z)

@@ -198,8 +198,8 @@ def sector_kernel_flops_per_eval(d: int) -> int:
     """FP64 work of one evaluation in the form the kernel runs for the sector benchmark
     workload (both polynomials dense, F in fixed point, d compiled in; qmc_poly.cuh): U's
     dense quadratic in V = d + 1 variables with the x_d = 1 iterations as additions
-    (V (V - 1) / 2 + V - 1 fma, V + 1 adds), the power U / (F^2 sqrt F) (3 mul, sqrt,
-    reciprocal), the weight (2 mul) and the accumulation (2 adds).  F's Horner form and the
+    (V (V - 1) / 2 + V - 1 fma, V + 1 adds), the power U (F^-1/2)^5 (a reciprocal square
+    root, 4 mul), the weight (2 mul) and the accumulation (2 adds).  F's Horner form and the
     Korobov map run on the integer pipe (sector_int_mul_per_eval)."""
     V = d + 1
     fma = V * (V - 1) // 2 + V - 1

@@ -543,15 +543,11 @@ __device__ __forceinline__ double pow_pos(double x, double y) {
     return pow(x, y);
 }
 
-// U^a F^-b of the real family: U / (F^n sqrt F) when a = 1, b = n + 1/2 and F > 0 (the
-// same products, square root and one division as pow_pos, without its tests on a and b),
-// else pow_pos.
+// U^a F^-b of the real family: U (F^-1/2)^(2n+1) when a = 1, b = n + 1/2 and F > 0 (one
+// reciprocal square root and its powers instead of a square root and a division; the
+// exponent tests made once at staging), else pow_pos.
 __device__ __forceinline__ double sector_power(double U, double F, const PolyShared &ps) {
-    if (ps.pow_half >= 0 && F > 0.0) {
-        double v = sqrt(F);
-        if (ps.pow_half) v *= ipow_u(F, ps.pow_half);
-        return U / v;
-    }
+    if (ps.pow_half >= 0 && F > 0.0) return U * ipow_u(rsqrt(F), 2 * ps.pow_half + 1);
     return pow_pos(U, ps.pa) * pow_pos(F, -ps.pb);
 }
 

@@ -276,8 +276,8 @@ __device__ __forceinline__ void stage_poly(const P &p, PolyShared &ps, bool allo
                 feyn_add_term(fb, fb + nU, p.fexp + (size_t)q * d, d, p.fcoef[q]);
             // Scales of the fixed-point form: with B the sum of |entries| of a polynomial's
             // tensors, every quantity feyn_fixed_parts forms at x in [0, 1]^d (Hessian
-            // entries, contractions, gradient, value, and their partial sums) is below
-            // (2d + 1) B <= 16 B, so c 2^s with 16 B 2^s < 2^62 cannot overflow.
+            // entries, contractions, gradients and their partial sums) is below 3 B, so
+            // with 16 B 2^s < 2^62 nothing can overflow.
             double bf = 0.0, bu = 0.0;
             for (int e = 0; e < nF; ++e) bf += fabs(fb[e]);
             for (int e = 0; e < nU; ++e) bu += fabs(ps.buf.v[e]);

@@ -143,3 +143,28 @@ def test_sector_work_counts():
                 adds += 1
         assert bench.sector_kernel_flops_per_eval(d) == 2 * fma + adds + 5 + 2 + 2
     assert len(bench.workload_items(0, None, "sector")) == bench.SECTOR_INTEGRALS
+
+
+def test_roofline_fractions_follow_from_the_counts():
+    """roofline() turns the per-step counts and the per-launch time into achieved rates
+    and fractions of the measured peaks, per workload (binding unit first)."""
+    pk = {"fp64_gflops": 1000.0, "int_mul_gops": 8000.0}
+    evals = 1e9                                   # per launch
+    for workload, key, per_eval in (("genz", "muls_per_step", 200),
+                                    ("feynman", "tensor_flops_per_step", 700),
+                                    ("sector", "tensor_flops_per_step", 100)):
+        r = {"unit_peaks": pk, "kernel_ms_per_launch": 500.0, "items": [0, 1],
+             "flops_per_step": 2 * evals * 50, "muls_per_step": 2 * evals * 300,
+             "tensor_flops_per_step": 2 * evals * per_eval}
+        if key == "muls_per_step":
+            r["muls_per_step"] = 2 * evals * per_eval
+        roof = bench.roofline(r, workload)
+        assert roof["bound"] == "alu"
+        rate = evals * per_eval / 0.5 / 1e9        # per second, G units
+        peak = pk["int_mul_gops"] if workload == "genz" else pk["fp64_gflops"]
+        assert roof["achieved"] == pytest.approx(rate, rel=1e-3)
+        assert roof["frac"] == pytest.approx(rate / peak, rel=1e-3)
+        assert roof["fp64_equivalent"]["frac"] == pytest.approx(evals * 50 / 0.5 / 1e9 / 1000.0, rel=1e-3)
+        if workload != "genz":
+            assert roof["int_pipe"]["frac"] == pytest.approx(evals * 300 / 0.5 / 1e9 / 8000.0, rel=1e-3)
+        assert (roof["traffic"] is not None) == (workload == "genz")

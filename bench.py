@@ -57,11 +57,11 @@ SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) of one lattice-sum launch from an ncu capture of the current
 # kernel, or None when the kernel has changed since the capture: sums_kernel<Gaussian,
-# integer Korobov>, d = 10, Korobov-3, n = 1,072,187, m = 32 (2272 tiles): 93,696 bytes
+# integer Korobov>, d = 10, Korobov-3, n = 1,072,187, m = 32 (2272 tiles): 98,560 bytes
 # read, 0 written (the partials stay in L2).  The inputs are kilobytes and the partials
 # grow only with the tile count (at most six waves of 760), so the figure stands for the
 # benchmark's launches.
-TRAFFIC_BYTES_PER_LAUNCH = 93_696
+TRAFFIC_BYTES_PER_LAUNCH = 98_560
 
 # 32-bit integer multiplies of the fixed-point primitives (qmc_fixed.cuh):
 MUL_HI = 3        # truncated 64-bit high product: one 32x32->64, two 32-bit high multiplies
